@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and the benchmark.
+
+This module draws random numbers and arranges them into raw (not yet
+projected) matrix fields.  It holds none of the MBO arithmetic: no heat
+multiplier, no transform, no projection.  Each consumer projects the raw field
+onto O_n with its own projection (the oracle's Jacobi SVD on the CPU, the
+library's kernel on the GPU), since Algorithm 1 takes an O_n-valued A_0.
+
+Layout: float64 array of shape ``(n*n, *dims)``; channel ``i*n+j`` is matrix
+entry ``(i, j)``; ``dims`` is row-major with the last axis (x) fastest.
+The torus is [0,1)^d with grid point index i_j at coordinate i_j / N_j.
+
+Workload recipes (the paper has no dataset; these stand in for its flat-torus
+experiments, Sec. 6.1, at the sizes the benchmark configurations name):
+  * ``gaussian``      iid N(0,1) entries per point.
+  * ``sign_split``    iid N(0,1) entries, conditioned so that det > 0 where
+                      x < 1/2 and det < 0 where x >= 1/2 (rows 0 and 1 of a
+                      matrix with the wrong sign are swapped; the swap is
+                      measure preserving, so entries stay N(0,1)).
+  * ``voronoi``       piecewise-constant Haar SO(3) rotations on seeded
+                      periodic Voronoi cells plus N(0, sd) entrywise noise.
+  * ``smooth_so3``    exp of a Gaussian random so(3) field with spectrum
+                      ~ exp(-|k|^2 / kc^2), some points replaced by -Q with
+                      Q Haar in SO(3) (determinant -1).
+  * ``batch_mixed``   many independent 2-D fields of uneven sizes and orders.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 171101365
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def gaussian(dims, n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """iid N(0,1) matrix entries at every grid point."""
+    g = rng(seed)
+    return g.standard_normal((n * n,) + tuple(int(d) for d in dims)).astype(dtype, copy=False)
+
+
+def _det_sign_sample(F: np.ndarray, n: int) -> np.ndarray:
+    """sign(det) of every point's raw matrix (input preparation only)."""
+    M = np.moveaxis(F.reshape((n, n) + F.shape[1:]), (0, 1), (-2, -1))
+    return np.sign(np.linalg.det(M))
+
+
+def sign_split(dims, n: int, seed: int) -> np.ndarray:
+    """iid N(0,1) entries; det > 0 on x < 1/2 and det < 0 on x >= 1/2."""
+    if n < 2:
+        raise ValueError("sign_split needs n >= 2")
+    F = gaussian(dims, n, seed)
+    nx = F.shape[-1]
+    want = np.where(np.arange(nx) < nx // 2, 1.0, -1.0)
+    have = _det_sign_sample(F, n)
+    wrong = have != want  # broadcast over the last axis
+    for j in range(n):  # swap rows 0 and 1 where the sign is wrong
+        c0, c1 = 0 * n + j, 1 * n + j
+        a = F[c0][wrong].copy()
+        F[c0][wrong] = F[c1][wrong]
+        F[c1][wrong] = a
+    return F
+
+
+def haar_so3(count: int, g: np.random.Generator) -> np.ndarray:
+    """Haar-random rotations from uniform unit quaternions (Shoemake 1992)."""
+    u1, u2, u3 = g.random(count), g.random(count), g.random(count)
+    a = np.sqrt(1 - u1)
+    b = np.sqrt(u1)
+    w = a * np.sin(2 * np.pi * u2)
+    x = a * np.cos(2 * np.pi * u2)
+    y = b * np.sin(2 * np.pi * u3)
+    z = b * np.cos(2 * np.pi * u3)
+    R = np.empty((count, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def voronoi(dims, seed: int, cells: int = 64, sd: float = 0.05, dtype=np.float64) -> np.ndarray:
+    """Piecewise-constant Haar SO(3) on periodic Voronoi cells + N(0, sd) noise (n = 3)."""
+    g = rng(seed)
+    d = len(dims)
+    centres = g.random((cells, d))
+    rots = haar_so3(cells, g)
+    shape = tuple(int(s) for s in dims)
+    P = int(np.prod(shape))
+    out = np.empty((9, P), dtype=dtype)
+    coords = [np.arange(s) / s for s in shape]
+    # process in slabs along the first axis to bound memory
+    plane = P // shape[0]
+    grid_rest = np.stack(np.meshgrid(*coords[1:], indexing="ij"), -1).reshape(-1, d - 1)
+    for i0 in range(shape[0]):
+        pts = np.concatenate([np.full((plane, 1), coords[0][i0]), grid_rest], axis=1)
+        best = np.full(plane, np.inf)
+        lab = np.zeros(plane, dtype=np.int64)
+        for c in range(cells):
+            diff = np.abs(pts - centres[c])
+            diff = np.minimum(diff, 1.0 - diff)  # minimum image on the unit torus
+            dist = (diff * diff).sum(1)
+            m = dist < best
+            best[m] = dist[m]
+            lab[m] = c
+        out[:, i0 * plane:(i0 + 1) * plane] = rots[lab].reshape(plane, 9).T
+    out += sd * g.standard_normal(out.shape)
+    return out.reshape((9,) + shape)
+
+
+def smooth_so3(dims, seed: int, kc: float = 32.0, frac_reflect: float = 0.2,
+               dtype=np.float32) -> np.ndarray:
+    """exp([w]_x) of a smooth Gaussian so(3) field; a Bernoulli(frac) mask of
+    points is replaced by -Q, Q Haar in SO(3) (n = 3, any d)."""
+    g = rng(seed)
+    shape = tuple(int(s) for s in dims)
+    P = int(np.prod(shape))
+    ks = np.meshgrid(*[np.fft.fftfreq(s, 1.0 / s) for s in shape], indexing="ij", sparse=True)
+    k2 = sum(k.astype(np.float64) ** 2 for k in ks)
+    amp = np.sqrt(np.exp(-k2 / kc ** 2))
+    w = np.empty((3, P), dtype=np.float64)
+    for i in range(3):
+        white = g.standard_normal(shape)
+        f = np.fft.ifftn(np.fft.fftn(white) * amp).real
+        f /= f.std()
+        w[i] = f.reshape(-1)
+    theta = np.sqrt((w * w).sum(0))
+    safe = np.where(theta > 0, theta, 1.0)
+    kx, ky, kz = w / safe
+    s, c1 = np.sin(theta), 1.0 - np.cos(theta)
+    R = np.empty((9, P), dtype=np.float64)
+    # Rodrigues: I + sin(t) K + (1 - cos(t)) K^2 for the unit axis (kx, ky, kz)
+    R[0] = 1 + c1 * (-(ky * ky + kz * kz))
+    R[1] = -s * kz + c1 * kx * ky
+    R[2] = s * ky + c1 * kx * kz
+    R[3] = s * kz + c1 * kx * ky
+    R[4] = 1 + c1 * (-(kx * kx + kz * kz))
+    R[5] = -s * kx + c1 * ky * kz
+    R[6] = -s * ky + c1 * kx * kz
+    R[7] = s * kx + c1 * ky * kz
+    R[8] = 1 + c1 * (-(kx * kx + ky * ky))
+    mask = g.random(P) < frac_reflect
+    cnt = int(mask.sum())
+    if cnt:
+        R[:, mask] = -haar_so3(cnt, g).reshape(cnt, 9).T
+    return R.astype(dtype).reshape((9,) + shape)
+
+
+# Batched 2-D workload: field i gets N = SIZES[i % 7], n = 2 + (i % 2), tau = 4 / N^2.
+BATCH_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
+
+
+def batch_mixed(count: int, seed: int, sizes=BATCH_SIZES):
+    """List of (dims, n, tau, raw field) for independent uneven 2-D fields."""
+    out = []
+    for i in range(count):
+        N = sizes[i % len(sizes)]
+        n = 2 + (i % 2)
+        out.append(((N, N), n, 4.0 / N ** 2, None if seed is None else (seed + 1000 + i)))
+    return out
+
+
+# Named workloads.  tau is in units of h^2 with h = 1 / N (Sec. 5.1 grid on [0,1)^d).
+CONFIGS = {
+    "C1": dict(dims=(128, 128), n=2, tau=4.0 / 128 ** 2, steps=100, init="gaussian"),
+    "C2": dict(dims=(1024, 1024), n=3, tau=3.0 / 1024 ** 2, steps=200, init="sign_split"),
+    "C3": dict(dims=(256, 256, 256), n=3, tau=2.0 / 256 ** 2, steps=300, init="voronoi"),
+    "C4": dict(count=96, steps=100, init="batch_mixed"),
+    "C5": dict(dims=(512, 512, 512), n=3, tau=2.0 / 512 ** 2, steps=100, init="smooth_so3"),
+}
+
+
+def config_field(name: str, seed: int | None = None, dims=None) -> tuple[np.ndarray, int, float]:
+    """Raw initial field for a named workload, optionally at smaller dims
+    (tau is rescaled to keep the same multiple of h^2)."""
+    cfg = CONFIGS[name]
+    seed = SEED_BASE + int(name[1:]) if seed is None else seed
+    d = tuple(dims) if dims is not None else cfg["dims"]
+    tau = cfg["tau"] * (cfg["dims"][-1] / d[-1]) ** 2
+    n = cfg["n"]
+    init = cfg["init"]
+    if init == "gaussian":
+        F = gaussian(d, n, seed)
+    elif init == "sign_split":
+        F = sign_split(d, n, seed)
+    elif init == "voronoi":
+        F = voronoi(d, seed)
+    elif init == "smooth_so3":
+        F = smooth_so3(d, seed, kc=32.0 * d[-1] / cfg["dims"][-1], dtype=np.float64)
+    else:
+        raise ValueError(init)
+    return F, n, tau
