@@ -1,0 +1,373 @@
+"""Benchmark of the flat-torus generalized MBO iteration on GB300.
+
+Workload (the single-GPU configuration the headline metric is quoted on):
+2-D torus 1024 x 1024, n = 3 (O_3-valued), tau = 3 h^2, initial field iid
+N(0,1) 3x3 entries with det > 0 on x < 1/2 and det < 0 on x >= 1/2, projected
+onto O_3.  A step is one MBO iteration (diffusion of all 9 channels,
+projection of every point, FP64 Lyapunov energy, stationarity statistics).
+The FP32 form is the headline ``value``; the FP64 form is reported beside it.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream with a 256 MB L2-flushing read between steps (outside
+the events); barrier + synchronize on both sides; max over ranks.  The field
+and its workspace (~80 MB) would otherwise stay in the 129 MB L2.
+
+Multi-GPU: the path has no exchange step; each rank iterates its own field
+(replicas, weak scaling, no collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_01365_gb300 import inputs as I  # noqa: E402
+
+METRIC = "grid-point MBO iterations/sec and % HBM roofline, FP32/batched vs FP64 plain"
+UNIT = "grid-point iterations/s"
+WORKLOAD = "C2"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def field_c2(dims=None):
+    F, n, tau = I.config_field(WORKLOAD, dims=dims)
+    return F, n, tau
+
+
+def oracle_sample(steps_budget_s: float, K: int | None = None):
+    """Time the FP64 oracle on the full workload, whole MBO iterations only."""
+    from oracle import oracle as O
+
+    F, n, tau = field_c2()
+    cores = O.set_threads(0)
+    A = O.project(F, n)
+    P = int(np.prod(F.shape[1:]))
+    done, t0 = 0, time.perf_counter()
+    times = []
+    while True:
+        ts = time.perf_counter()
+        A, _ = O.step(A, n, tau)
+        times.append(time.perf_counter() - ts)
+        done += 1
+        el = time.perf_counter() - t0
+        if (K is not None and done >= K) or (K is None and el >= steps_budget_s) or el >= steps_budget_s:
+            break
+    total = sum(times)
+    return {"value": P * done / total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} full MBO iteration(s) of the {F.shape[1]}x{F.shape[2]} n={n} field, "
+                      f"FP64 C oracle, OpenMP over {cores} threads",
+            "steps": done, "seconds": total}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    F, n, tau = field_c2()
+    P = int(np.prod(F.shape[1:]))
+    cores = O.set_threads(0)
+    A = O.project(F, n)
+    for _ in range(args.warmup):
+        A, _ = O.step(A, n, tau)
+    budget = 150.0
+    times = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ts = time.perf_counter()
+        A, _ = O.step(A, n, tau)
+        times.append(time.perf_counter() - ts)
+        if time.perf_counter() - t0 > budget:
+            break
+    total = sum(times)
+    done = len(times)
+    v = P * done / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2-D flat torus 1024x1024, n=3, tau=3h^2, sign-split iid N(0,1) init",
+                   "grid": list(F.shape[1:]), "n": n, "tau": tau},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} of {args.steps} requested full MBO iterations "
+                                   f"(time budget {budget:.0f} s), FP64 C oracle, {cores} threads"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(torch, h, A, K, flush, prof=True):
+    """K steady-state steps, each between CUDA events, L2 flushed in between."""
+    from paper_1711_01365_gb300 import mbo as M
+
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if prof:
+        M.mbo_profile_enable(h.h, True)
+    for k in range(K):
+        flush()
+        ev[k][0].record(s)
+        h.step(A, flags=M.MBO_STEP_CONTINUE)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    passes = M.mbo_profile_read(h.h) if prof else None
+    if prof:
+        M.mbo_profile_enable(h.h, False)
+    return ms, passes
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1711_01365_gb300 import build as B
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_1711_01365_gb300 import mbo as M
+
+    F, n, tau = field_c2()
+    dims = tuple(F.shape[1:])
+    P = int(np.prod(dims))
+    C = n * n
+    # initial field: projected onto O_3 by the library (FP64)
+    raw = torch.tensor(F, dtype=torch.float64, device="cuda")
+    h64 = M.Mbo(dims, n, tau, "f64")
+    A0 = torch.empty_like(raw)
+    h64.project(raw, A0)
+    del raw
+    flushbuf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+    flushbuf.fill_(1.0)
+    sink = torch.zeros((), dtype=torch.float32, device="cuda")
+
+    def flush():
+        sink.add_(flushbuf.sum())
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- FP32 form (headline) ----
+    h32 = M.Mbo(dims, n, tau, "f32")
+    A32 = A0.float().contiguous()
+    h32.step(A32)  # fills the workspace spectrum
+    for _ in range(max(args.warmup - 1, 0)):
+        flush()
+        h32.step(A32, flags=M.MBO_STEP_CONTINUE)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ms32, passes = time_steps(torch, h32, A32, args.steps, flush)
+    clocks = clk.stop()
+    barrier()
+    t32 = sum(ms32) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t32], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t32 = float(tt.item())
+    value = P * args.steps * ws / t32
+
+    # dominant kernel: the fused inverse-x / projection / forward-x pass
+    hbm, peak_kind = load_peaks()
+    elem = 4
+    Q = (C + 1) // 2
+    w_bytes = Q * P * 2 * elem
+    a_bytes = C * P * elem
+    row_ms, row_n = passes["row_project"]
+    ax_ms, ax_n = passes["axis_fgi"]
+    row_alg = 2 * w_bytes + 2 * a_bytes  # read W, read old A, write A, write W
+    ax_alg = 2 * w_bytes                 # read W, write W
+    row_t = row_ms / 1e3 / max(row_n, 1)
+    ax_t = ax_ms / 1e3 / max(ax_n, 1)
+    dominant = ("row_project", row_alg, row_t) if row_ms >= ax_ms else ("axis_fgi", ax_alg, ax_t)
+    achieved = dominant[1] / dominant[2] / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": None,
+                "alg_bytes_per_launch": dominant[1], "launch_us": dominant[2] * 1e6,
+                "passes_us": {"row_project": row_t * 1e6, "axis_fgi": ax_t * 1e6},
+                "step_alg_bytes": row_alg + ax_alg,
+                "step_frac": (row_alg + ax_alg) / (t32 / args.steps) / 1e9 / hbm}
+
+    # ---- FP64 form (plain), same workload ----
+    fp64 = None
+    if not args.no_fp64:
+        A64 = A0.clone()
+        h64.step(A64)
+        for _ in range(2):
+            h64.step(A64, flags=M.MBO_STEP_CONTINUE)
+        K64 = max(3, min(args.steps, 10))
+        barrier()
+        ms64, p64 = time_steps(torch, h64, A64, K64, flush)
+        barrier()
+        t64 = sum(ms64) / 1e3
+        fp64 = {"value": P * K64 * ws / t64, "unit": UNIT, "steps": K64,
+                "ms_per_step": 1e3 * t64 / K64,
+                "passes_us": {k: 1e3 * v[0] / max(v[1], 1) for k, v in p64.items() if v[1]}}
+
+    # ---- run loop as a user runs it (graph replay, L2 left warm) ----
+    Arun = A0.float().contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = h32.run(Arun, args.run_steps, -1.0)
+    t_run = time.perf_counter() - t0
+    run_loop = {"value": P * r["steps"] / t_run, "unit": UNIT, "steps": r["steps"],
+                "note": "mbo_run_until_stationary on a device field, wall clock, L2 not flushed"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    hostA = A0.float().cpu().pin_memory()
+    e2e_times = []
+    for _ in range(3):
+        src = hostA.clone().pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = h32.run(src, args.run_steps, -1.0)
+        e2e_times.append(time.perf_counter() - t0)
+    te = float(np.median(e2e_times))
+    fbytes = a_bytes
+    e2e = {"value": P * args.run_steps * ws / te, "unit": UNIT,
+           "h2d_bytes_per_step": fbytes / args.run_steps,
+           "d2h_bytes_per_step": (fbytes + 8 * (args.run_steps + 1)) / args.run_steps,
+           "steps_per_call": args.run_steps,
+           "note": "mbo_run_until_stationary on a pinned host field: H2D, all iterations, D2H"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_sample(args.cpu_seconds)
+        cpu.pop("steps", None)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "2-D flat torus 1024x1024, n=3 (O_3), tau=3h^2, sign-split "
+                                   "iid N(0,1) init projected; FP32 form with FP64 energy and "
+                                   "FP64 re-projection where sigma_min<1e-3",
+                       "grid": list(dims), "n": n, "tau": tau,
+                       "l2": "flushed between timed steps (256 MB read)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": sum(v[1] for v in passes.values()),
+            "clocks": clocks,
+            "fp64": fp64,
+            "run_loop": run_loop,
+        }
+        print(json.dumps(line), flush=True)
+    h32.close()
+    h64.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--run-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

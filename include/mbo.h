@@ -1,0 +1,174 @@
+/*
+ * mbo.h - C ABI of the GB300 (sm_103a) generalized MBO library.
+ *
+ * The library runs Algorithm 1 ("a:MBO") of Osting & Wang, "A generalized MBO
+ * diffusion generated motion for orthogonal matrix-valued fields"
+ * (arXiv:1711.01365) on a flat torus [0,1)^d, d = 2 or 3:
+ *   diffusion  (Sec. 5.1): every entry A_ij is advanced by the periodic heat
+ *              semigroup, A~ = iFFT( g(k) FFT(A_ij) ), g(k) = exp(-4 pi^2 tau |k|^2);
+ *   projection (Lemma 2.1): every grid point becomes U V^t, the closest
+ *              orthogonal matrix to A~(x) = U S V^t, whose determinant has the
+ *              sign of det A~(x) (det A~ = 0 -> +1; A~ = 0 -> identity);
+ *   Lyapunov functional (Eq. 4.1): E(A) = (prod h_j / tau) sum_x (n - <A, e^{tau Lap} A>_F);
+ *   stationarity (Prop. 4.6): a step is stationary when no point changes its
+ *              determinant sign and every entry moves by at most tol.
+ *
+ * Conventions shared by every entry point
+ *   - Fields are planar arrays of n*n channels: channel c = i*n + j holds matrix
+ *     entry (i,j); each channel is a row-major block of P = prod(dims) values
+ *     with the last axis (x) fastest.  dims is {Ny, Nx} (d = 2) or
+ *     {Nz, Ny, Nx} (d = 3).  Element type: float (MBO_F32) or double (MBO_F64),
+ *     as given to mbo_create.
+ *   - Field pointers are CALLER-OWNED device pointers, 16-byte aligned, unless
+ *     an entry point says otherwise.  The library never frees them.
+ *   - stream is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls are asynchronous on that stream unless they return a
+ *     value on the host (documented per call).
+ *   - Every entry point returns an mbo_status; nothing is thrown.  Device-side
+ *     problems (non-finite values, a wait that gave up) are recorded in the
+ *     handle and reported by the next call that synchronises.
+ *   - A handle is not thread safe; distinct handles are independent.
+ *   - Supported sizes: every N_j = 2^a 3^b with 2 <= N_j <= 2048; n in {1,2,3};
+ *     other sizes return MBO_ERR_UNSUPPORTED_SIZE.
+ */
+#ifndef MBO_GB300_H
+#define MBO_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MBO_API __attribute__((visibility("default")))
+#else
+#define MBO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbo_ctx* mbo_handle;
+
+typedef enum { MBO_F32 = 1, MBO_F64 = 2 } mbo_dtype;
+
+typedef enum {
+  MBO_OK = 0,
+  MBO_ERR_INVALID_ARG = 1,      /* null/misaligned pointer, bad n, tau <= 0, ... */
+  MBO_ERR_UNSUPPORTED_SIZE = 2, /* an axis length outside 2^a 3^b in [2, 2048]   */
+  MBO_ERR_OOM = 3,              /* device allocation failed                       */
+  MBO_ERR_CUDA = 4,             /* a CUDA runtime call failed (see mbo_last_error) */
+  MBO_ERR_NUMERIC = 5,          /* NaN or Inf met in the projected field          */
+  MBO_ERR_DEVICE_TIMEOUT = 6    /* a bounded device-side wait gave up             */
+} mbo_status;
+
+/* Options; mbo_default_config fills the defaults. */
+typedef struct {
+  double fallback_sigma; /* MBO_F32: points whose smallest singular value of A~
+                            is below this are re-projected in FP64 from the FP32
+                            A~ (default 1e-3; <= 0 disables).  Ignored for F64. */
+  int check_interval;    /* run loop: the host reads the step records every this
+                            many steps to test for stationarity (default 16).    */
+  int use_graph;         /* run loop: replay the step from a captured CUDA graph
+                            (default 1).                                          */
+} mbo_config;
+
+/* Per-step record.  Step s maps A_{s} to A_{s+1}. */
+typedef struct {
+  double energy;           /* E^tau(A_s), accumulated in FP64 (Eq. 4.1)          */
+  double max_delta;        /* max over points and channels |A_{s+1} - A_s|        */
+  int64_t det_flips;       /* points where sign det A_{s+1} != sign det A_s       */
+  int64_t fallback_points; /* MBO_F32: points re-projected in FP64                */
+  int64_t nonfinite;       /* points whose projection is not finite               */
+} mbo_stats;
+
+MBO_API void mbo_default_config(mbo_config* cfg);
+
+/* Create a handle for one field geometry.
+ *   out   receives the handle (set to NULL on failure).
+ *   ndim  2 or 3; dims[ndim] as in the conventions above.
+ *   n     matrix order (1, 2 or 3); tau > 0 the diffusion time of one step.
+ *   cfg   NULL for the defaults.
+ * Allocates the spectral workspace (ceil(n*n/2) complex planes of P points)
+ * and small tables on the current device.  Synchronous. */
+MBO_API mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, double tau,
+                      mbo_dtype dtype, const mbo_config* cfg);
+
+/* Release the handle and everything it allocated.  Synchronises the device. */
+MBO_API mbo_status mbo_destroy(mbo_handle h);
+
+/* Diffusion step of Algorithm 1 alone (Sec. 5.1): A_tilde = e^{tau Lap} A.
+ * A and A_tilde are device fields (they may be the same pointer). */
+MBO_API mbo_status mbo_diffuse(mbo_handle h, const void* A, void* A_tilde, void* stream);
+
+/* Projection step of Algorithm 1 alone (Lemma 2.1): B(x) = polar factor of
+ * A_tilde(x).  det_sign (nullable, int8 per point) receives +1 or -1, the
+ * class chosen for B.  A_tilde and B may be the same pointer. */
+MBO_API mbo_status mbo_project(mbo_handle h, const void* A_tilde, void* B, int8_t* det_sign,
+                       void* stream);
+
+/* Flag for mbo_step: the field is the one the previous mbo_step (or run) on
+ * this handle left, unmodified since; its forward row transform, kept in the
+ * workspace, is reused and one of the three transform passes is skipped. */
+#define MBO_STEP_CONTINUE 1
+
+/* One iteration of Algorithm 1 in place: A <- polar(e^{tau Lap} A), fused
+ * (transform passes, heat multiplier, projection, energy, statistics).
+ * stats (nullable): if given, the call synchronises the stream and fills the
+ * record of this step (energy is that of the input field). */
+MBO_API mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* stream);
+
+/* Lyapunov functional E^tau(A) (Eq. 4.1), in its Parseval form
+ *   (1/(P tau)) [ (1/P) sum_k (1 - g(k)) sum_c |A^_c(k)|^2 + sum_x (n - |A(x)|_F^2) ],
+ * accumulated in FP64.  Synchronises the stream; result in *E. */
+MBO_API mbo_status mbo_lyapunov(mbo_handle h, const void* A, double* E, void* stream);
+
+/* Iterate Algorithm 1 in place until a step is stationary (no determinant
+ * sign flips and max |A_{s+1} - A_s| <= tol) or max_steps steps were taken.
+ * A may be a device pointer or a host pointer (pageable or pinned); for a host
+ * pointer the field is copied to the device, iterated, and copied back.
+ * Outputs (all nullable):
+ *   steps_taken  number of steps performed;
+ *   stationary   1 if the last step was stationary, else 0;
+ *   energies     [max_steps + 1]: E^tau(A_0) ... E^tau(A_steps);
+ *   max_deltas   [max_steps]: per-step max |A_{s+1} - A_s|;
+ *   det_flips    [max_steps]: per-step determinant sign flips;
+ *   last         record of the last step.
+ * tol < 0 never stops early.  Synchronises the stream before returning. */
+MBO_API mbo_status mbo_run_until_stationary(mbo_handle h, void* A, int max_steps, double tol,
+                                    int* steps_taken, int* stationary, double* energies,
+                                    double* max_deltas, int64_t* det_flips, mbo_stats* last,
+                                    void* stream);
+
+/* Per-pass device timing.  While enabled, every kernel pass launched through
+ * this handle is bracketed by CUDA events on its stream (the run loop then
+ * launches directly instead of replaying its graph).  mbo_profile_enable
+ * (re)starts the accumulation; mbo_profile_read synchronises on the recorded
+ * events and returns, per pass id below, the summed milliseconds and the
+ * number of launches (arrays of length npass, nullable). */
+enum {
+  MBO_PASS_ROW_FWD = 0,      /* forward x transform of a field                 */
+  MBO_PASS_AXIS_FWD = 1,     /* forward y transform (3-D)                      */
+  MBO_PASS_AXIS_FGI = 2,     /* last axis: forward, heat multiplier, inverse   */
+  MBO_PASS_AXIS_INV = 3,     /* inverse y transform (3-D)                      */
+  MBO_PASS_AXIS_ENERGY = 4,  /* last axis: forward + energy only               */
+  MBO_PASS_ROW_PROJECT = 5,  /* inverse x, projection, statistics, forward x   */
+  MBO_PASS_ROW_INV = 6,      /* inverse x to a real field (mbo_diffuse)        */
+  MBO_PASS_PROJECT = 7,      /* pointwise projection (mbo_project)             */
+  MBO_PROFILE_PASSES = 8
+};
+MBO_API mbo_status mbo_profile_enable(mbo_handle h, int enable);
+MBO_API mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npass);
+
+/* Bytes of device memory the handle holds (workspace and tables). */
+MBO_API int64_t mbo_workspace_bytes(mbo_handle h);
+
+/* Human-readable text for a status code (static storage). */
+MBO_API const char* mbo_status_string(mbo_status s);
+
+/* Text of the last error recorded in the handle (empty string if none). */
+MBO_API const char* mbo_last_error(mbo_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBO_GB300_H */

@@ -1,0 +1,735 @@
+// Host side of the C ABI declared in include/mbo.h: validation, radix plans,
+// twiddle and heat-multiplier tables, workspace ownership, the launch
+// sequences of the diffusion / projection / step / energy calls, and the run
+// loop (CUDA-graph replay of one step, host polling of the device step
+// records every few steps).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mbo.h"
+#include "mbo_dev.cuh"
+#include "mbo_internal.h"
+
+namespace mbo {
+
+size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback) {
+  size_t b = (size_t)g.Q * (size_t)row_pad(g.nx) * 2 * elem_bytes;
+  if (fallback) b += (size_t)kFallbackCap * ((size_t)g.C * sizeof(float) + sizeof(int));
+  return (b + 15) & ~(size_t)15;
+}
+size_t axis_smem_bytes(int len, int tx, size_t elem_bytes) { return (size_t)len * tx * 2 * elem_bytes; }
+
+}  // namespace mbo
+
+using namespace mbo;
+
+struct mbo_ctx {
+  int dev = 0;
+  Geom g{};
+  int64_t dims_user[3] = {0, 0, 0};
+  mbo_dtype dtype = MBO_F32;
+  mbo_config cfg{};
+  size_t elem = 4;
+  // device memory
+  void* W = nullptr;
+  void* tabs = nullptr;  // twiddles, multipliers (one allocation)
+  size_t tabs_bytes = 0;
+  double* part = nullptr;
+  RunState* st = nullptr;
+  Hist hist{};
+  void* hist_mem = nullptr;
+  void* field = nullptr;  // staging field for host-pointer runs
+  // host mirrors
+  RunState* h_st = nullptr;  // pinned
+  void* h_hist = nullptr;    // pinned ring copy
+  // launch configuration
+  Tables<float> tf{};
+  Tables<double> td{};
+  int row_threads = 256, axis_threads = 256, tx = 8;
+  size_t bytes_total = 0;
+  // workspace validity for MBO_STEP_CONTINUE
+  const void* w_valid_for = nullptr;
+  // captured step graph
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_ptr = nullptr;
+  double g_tol = 0;
+  // per-pass device timing (mbo_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pending { int pass; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double prof_ms[MBO_PROFILE_PASSES] = {0};
+  long long prof_n[MBO_PROFILE_PASSES] = {0};
+  char err[512] = {0};
+};
+
+namespace {
+
+mbo_status fail(mbo_ctx* h, mbo_status s, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? MBO_ERR_OOM : MBO_ERR_CUDA,        \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool factor23(int64_t N, int& a, int& b) {
+  a = b = 0;
+  while (N % 2 == 0) { N /= 2; ++a; }
+  while (N % 3 == 0) { N /= 3; ++b; }
+  return N == 1;
+}
+
+FastDiv make_div(unsigned d) {
+  FastDiv f{};
+  if ((d & (d - 1)) == 0) {
+    f.shift = 0;
+    while ((1u << f.shift) < d) ++f.shift;
+    f.mul = 0;
+  } else {
+    f.shift = -1;
+    f.mul = (unsigned)((((unsigned long long)1 << 32) + d - 1) / d);
+  }
+  return f;
+}
+
+// Radix plan: the power of two in ceil(a/4) stages of 16 / 8 / 4 / 2 (bits
+// spread evenly, larger radices first), then one radix-3 stage per factor 3.
+// Stage twiddle offsets are assigned in stage order.
+Plan make_plan(int N) {
+  Plan p{};
+  int a, b;
+  factor23(N, a, b);
+  int rad[kMaxStages];
+  int ns = 0;
+  if (a > 0) {
+    const int n2 = (a + 3) / 4;
+    for (int i = 0; i < n2; ++i) rad[ns++] = 1 << (a / n2 + (i < a % n2 ? 1 : 0));
+  }
+  for (int i = 0; i < b; ++i) rad[ns++] = 3;
+  p.nst = ns;
+  int lb = N, tw = 0;
+  for (int i = 0; i < ns; ++i) {
+    Stage& s = p.st[i];
+    s.rad = rad[i];
+    s.lb = lb;
+    s.m = lb / rad[i];
+    s.dm = make_div((unsigned)s.m);
+    s.dnr = make_div((unsigned)(N / rad[i]));
+    s.tw = tw;
+    if (s.m > 1) tw += s.m * (s.rad - 1);
+    lb /= rad[i];
+  }
+  return p;
+}
+
+int plan_twiddles(const Plan& p) {
+  int n = 0;
+  for (int i = 0; i < p.nst; ++i)
+    if (p.st[i].m > 1) n += p.st[i].m * (p.st[i].rad - 1);
+  return n;
+}
+
+// pos[k]: digit-reversed position where the forward network leaves frequency k.
+void digit_positions(const Plan& p, int N, std::vector<int>& pos) {
+  pos.assign(N, 0);
+  for (int k = 0; k < N; ++k) {
+    int kk = k, len = N, off = 0;
+    for (int st = 0; st < p.nst; ++st) {
+      const int r = p.st[st].rad;
+      const int M = len / r;
+      off += M * (kk % r);
+      kk /= r;
+      len = M;
+    }
+    pos[k] = off;
+  }
+}
+
+// Blocks along x per axis tile: largest power of two dividing nx, capped.
+int pick_tx(int nx, int cap) {
+  int t = 1;
+  while (t < cap && nx % (2 * t) == 0) t *= 2;
+  return t;
+}
+
+template <typename R> struct TabBuild {
+  std::vector<unsigned char> bytes;
+  size_t off_tw[3], off_g[3], off_om[3];
+};
+
+template <typename R>
+void build_tables(mbo_ctx* h, TabBuild<R>& tb, Tables<R>& t) {
+  const int lens[3] = {h->g.nx, h->g.ny, h->g.nz};
+  size_t off = 0;
+  auto reserve = [&](size_t n) {
+    size_t o = (off + 255) & ~(size_t)255;
+    off = o + n;
+    return o;
+  };
+  for (int ax = 0; ax < 3; ++ax) {
+    const int N = lens[ax];
+    t.plan[ax] = make_plan(N);
+    tb.off_tw[ax] = reserve((size_t)std::max(plan_twiddles(t.plan[ax]), 1) * 2 * sizeof(R));
+    tb.off_g[ax] = reserve((size_t)N * sizeof(R));
+    tb.off_om[ax] = reserve((size_t)N * sizeof(R));
+  }
+  tb.bytes.assign(off, 0);
+  const double pi = 3.14159265358979323846;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int N = lens[ax];
+    const Plan& pl = t.plan[ax];
+    R* tw = reinterpret_cast<R*>(&tb.bytes[tb.off_tw[ax]]);
+    for (int st = 0; st < pl.nst; ++st) {
+      const Stage& s = pl.st[st];
+      if (s.m <= 1) continue;
+      for (int n1 = 0; n1 < s.m; ++n1)
+        for (int j = 1; j < s.rad; ++j) {
+          const long long e = ((long long)n1 * j) % s.lb;
+          const double ang = 2.0 * pi * (double)e / (double)s.lb;
+          const size_t i = (size_t)s.tw + (size_t)n1 * (s.rad - 1) + (j - 1);
+          tw[2 * i] = (R)std::cos(ang);
+          tw[2 * i + 1] = (R)(-std::sin(ang));
+        }
+    }
+    std::vector<int> pos;
+    digit_positions(pl, N, pos);
+    R* gt = reinterpret_cast<R*>(&tb.bytes[tb.off_g[ax]]);
+    R* om = reinterpret_cast<R*>(&tb.bytes[tb.off_om[ax]]);
+    for (int k = 0; k < N; ++k) {
+      const double kf = (2 * k <= N) ? (double)k : (double)(k - N);
+      const double e = -4.0 * pi * pi * h->g.tau * kf * kf;
+      gt[pos[k]] = (R)std::exp(e);
+      om[pos[k]] = (R)(-std::expm1(e));
+    }
+  }
+  t.inv_p = (R)(1.0 / (double)h->g.P);
+}
+
+template <typename R> void bind_tables(mbo_ctx* h, const TabBuild<R>& tb, Tables<R>& t) {
+  const char* base = static_cast<const char*>(h->tabs);
+  for (int ax = 0; ax < 3; ++ax) {
+    t.tw[ax] = base + tb.off_tw[ax];
+    t.g[ax] = reinterpret_cast<const R*>(base + tb.off_g[ax]);
+    t.om[ax] = reinterpret_cast<const R*>(base + tb.off_om[ax]);
+  }
+}
+
+StatsPtrs stats_ptrs(mbo_ctx* h, bool stats, bool respect_stop, double tol) {
+  StatsPtrs sp{};
+  sp.st = h->st;
+  sp.hist = h->hist;
+  sp.part = h->part;
+  sp.respect_stop = respect_stop ? 1 : 0;
+  sp.do_stats = stats ? 1 : 0;
+  sp.tol = tol;
+  return sp;
+}
+
+cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout,
+                       const StatsPtrs& sp, cudaStream_t s);
+cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s);
+
+cudaEvent_t take_event(mbo_ctx* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch f on stream s; when profiling, bracket it with events (pass id).
+template <class F> cudaError_t timed(mbo_ctx* h, int pass, cudaStream_t s, F&& f) {
+  if (!h->prof) return f();
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  cudaEventRecord(a, s);
+  cudaError_t e = f();
+  cudaEventRecord(b, s);
+  h->pending.push_back({pass, a, b});
+  return e;
+}
+
+cudaError_t row_pass(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, const StatsPtrs& sp,
+                     cudaStream_t s) {
+  const int pass = mode == ROW_FWD ? MBO_PASS_ROW_FWD
+                   : mode == ROW_INV_OUT ? MBO_PASS_ROW_INV : MBO_PASS_ROW_PROJECT;
+  return timed(h, pass, s, [&]() { return row_launch(h, mode, Ain, Aout, sp, s); });
+}
+
+cudaError_t axis_pass(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s) {
+  const int pass = mode == AXIS_FWD ? MBO_PASS_AXIS_FWD
+                   : mode == AXIS_INV ? MBO_PASS_AXIS_INV
+                   : mode == AXIS_FGI ? MBO_PASS_AXIS_FGI : MBO_PASS_AXIS_ENERGY;
+  return timed(h, pass, s, [&]() { return axis_launch(h, mode, axis, sp, s); });
+}
+
+cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, const StatsPtrs& sp,
+                       cudaStream_t s) {
+  if (h->dtype == MBO_F32)
+    return launch_row<float>(mode, h->g, h->tf, static_cast<const float*>(Ain),
+                             static_cast<float*>(Aout), h->W, sp, h->cfg.fallback_sigma,
+                             h->row_threads, s);
+  return launch_row<double>(mode, h->g, h->td, static_cast<const double*>(Ain),
+                            static_cast<double*>(Aout), h->W, sp, 0.0, h->row_threads, s);
+}
+
+cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s) {
+  if (h->dtype == MBO_F32)
+    return launch_axis<float>(mode, axis, h->g, h->tf, h->W, sp, h->tx, h->axis_threads, s);
+  return launch_axis<double>(mode, axis, h->g, h->td, h->W, sp, h->tx, h->axis_threads, s);
+}
+
+// Transform passes between the forward and the inverse x pass.
+// mode AXIS_FGI: diffuse; AXIS_ENERGY: energy only (workspace not restored in 3-D).
+cudaError_t middle_passes(mbo_ctx* h, AxisMode mode, const StatsPtrs& sp, cudaStream_t s) {
+  const StatsPtrs none = [&] {
+    StatsPtrs n = sp;
+    n.do_stats = 0;
+    return n;
+  }();
+  cudaError_t e;
+  if (h->g.ndim == 2) return axis_pass(h, mode, 1, sp, s);
+  if ((e = axis_pass(h, AXIS_FWD, 1, none, s)) != cudaSuccess) return e;
+  if ((e = axis_pass(h, mode, 2, sp, s)) != cudaSuccess) return e;
+  if (mode == AXIS_FGI) return axis_pass(h, AXIS_INV, 1, none, s);
+  return cudaSuccess;
+}
+
+// The steady-state step: middle passes + inverse x / projection / forward x.
+cudaError_t step_passes(mbo_ctx* h, void* A, bool respect_stop, double tol, cudaStream_t s) {
+  const StatsPtrs sp = stats_ptrs(h, true, respect_stop, tol);
+  cudaError_t e = middle_passes(h, AXIS_FGI, sp, s);
+  if (e != cudaSuccess) return e;
+  return row_pass(h, ROW_INV_PROJECT_FWD, nullptr, A, sp, s);
+}
+
+mbo_status check_field_ptr(mbo_ctx* h, const void* p, const char* what) {
+  if (!p) return fail(h, MBO_ERR_INVALID_ARG, "%s is NULL", what);
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+    return fail(h, MBO_ERR_INVALID_ARG, "%s is not 16-byte aligned", what);
+  return MBO_OK;
+}
+
+void invalidate_graph(mbo_ctx* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->g_ptr = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mbo_status_string(mbo_status s) {
+  switch (s) {
+    case MBO_OK: return "ok";
+    case MBO_ERR_INVALID_ARG: return "invalid argument";
+    case MBO_ERR_UNSUPPORTED_SIZE: return "unsupported size (axis length must be 2^a 3^b in [2, 2048])";
+    case MBO_ERR_OOM: return "device out of memory";
+    case MBO_ERR_CUDA: return "CUDA error";
+    case MBO_ERR_NUMERIC: return "non-finite values in the field";
+    case MBO_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* mbo_last_error(mbo_handle h) { return h ? h->err : ""; }
+
+void mbo_default_config(mbo_config* cfg) {
+  if (!cfg) return;
+  cfg->fallback_sigma = 1e-3;
+  cfg->check_interval = 16;
+  cfg->use_graph = 1;
+}
+
+int64_t mbo_workspace_bytes(mbo_handle h) { return h ? (int64_t)h->bytes_total : 0; }
+
+mbo_status mbo_destroy(mbo_handle h) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(h->dev);
+  cudaDeviceSynchronize();
+  invalidate_graph(h);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->ev_free) cudaEventDestroy(e);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  cudaFree(h->W);
+  cudaFree(h->tabs);
+  cudaFree(h->part);
+  cudaFree(h->st);
+  cudaFree(h->hist_mem);
+  cudaFree(h->field);
+  cudaFreeHost(h->h_st);
+  cudaFreeHost(h->h_hist);
+  delete h;
+  return MBO_OK;
+}
+
+mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, double tau,
+                      mbo_dtype dtype, const mbo_config* cfg) {
+  if (!out) return MBO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((ndim != 2 && ndim != 3) || !dims || n < 1 || n > 3 || !(tau > 0) || !std::isfinite(tau) ||
+      (dtype != MBO_F32 && dtype != MBO_F64))
+    return MBO_ERR_INVALID_ARG;
+  for (int i = 0; i < ndim; ++i) {
+    int a, b;
+    if (dims[i] < 2 || dims[i] > 2048 || !factor23(dims[i], a, b)) return MBO_ERR_UNSUPPORTED_SIZE;
+  }
+  mbo_ctx* h = new mbo_ctx();
+  if (cfg) h->cfg = *cfg;
+  else mbo_default_config(&h->cfg);
+  if (h->cfg.check_interval < 1) h->cfg.check_interval = 1;
+  if (h->cfg.check_interval > kRing / 2) h->cfg.check_interval = kRing / 2;
+  h->dtype = dtype;
+  h->elem = dtype == MBO_F32 ? 4 : 8;
+  Geom& g = h->g;
+  g.ndim = ndim;
+  g.nx = (int)dims[ndim - 1];
+  g.ny = (int)dims[ndim - 2];
+  g.nz = ndim == 3 ? (int)dims[0] : 1;
+  for (int i = 0; i < ndim; ++i) h->dims_user[i] = dims[i];
+  g.P = (long long)g.nx * g.ny * g.nz;
+  g.n = n;
+  g.C = n * n;
+  g.Q = (g.C + 1) / 2;
+  g.tau = tau;
+  cudaGetDevice(&h->dev);
+  // launch shapes
+  h->tx = pick_tx(g.nx, dtype == MBO_F32 ? 8 : 4);
+  h->row_threads = g.nx >= 1024 ? 256 : (g.nx >= 256 ? 128 : (g.nx >= 64 ? 64 : 32));
+  h->axis_threads = 256;
+  const size_t rs = row_smem_bytes(g, h->elem, true);
+  const size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+  if (rs > (size_t)maxsm || as > (size_t)maxsm) {
+    delete h;
+    return MBO_ERR_UNSUPPORTED_SIZE;
+  }
+  mbo_status rc = MBO_OK;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      rc = MBO_ERR_OOM;
+      return false;
+    }
+    h->bytes_total += bytes;
+    return true;
+  };
+  const size_t wbytes = (size_t)g.Q * (size_t)g.P * 2 * h->elem;
+  const int rows = g.nz * g.ny;
+  const int tiles = g.Q * std::max(g.nz, g.ny) * (g.nx / h->tx);
+  const size_t nparts = (size_t)std::max(rows, tiles);
+  if (!alloc(&h->W, wbytes) || !alloc((void**)&h->part, nparts * sizeof(double)) ||
+      !alloc((void**)&h->st, sizeof(RunState)) ||
+      !alloc(&h->hist_mem, (size_t)kRing * 5 * sizeof(double))) {
+    mbo_destroy(h);
+    return rc;
+  }
+  char* hm = static_cast<char*>(h->hist_mem);
+  h->hist.energy = reinterpret_cast<double*>(hm);
+  h->hist.maxdelta = reinterpret_cast<double*>(hm + kRing * 8);
+  h->hist.flips = reinterpret_cast<long long*>(hm + 2 * kRing * 8);
+  h->hist.fallback = reinterpret_cast<long long*>(hm + 3 * kRing * 8);
+  h->hist.nonfinite = reinterpret_cast<long long*>(hm + 4 * kRing * 8);
+  if (dtype == MBO_F32) {
+    TabBuild<float> tb;
+    build_tables(h, tb, h->tf);
+    if (!alloc(&h->tabs, tb.bytes.size())) { mbo_destroy(h); return rc; }
+    cudaMemcpy(h->tabs, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice);
+    bind_tables(h, tb, h->tf);
+  } else {
+    TabBuild<double> tb;
+    build_tables(h, tb, h->td);
+    if (!alloc(&h->tabs, tb.bytes.size())) { mbo_destroy(h); return rc; }
+    cudaMemcpy(h->tabs, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice);
+    bind_tables(h, tb, h->td);
+  }
+  if (cudaMemset(h->st, 0, sizeof(RunState)) != cudaSuccess ||
+      cudaMemset(h->hist_mem, 0, (size_t)kRing * 5 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_st, sizeof(RunState)) != cudaSuccess ||
+      cudaMallocHost(&h->h_hist, (size_t)kRing * 5 * sizeof(double)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    mbo_destroy(h);
+    return MBO_ERR_CUDA;
+  }
+  *out = h;
+  return MBO_OK;
+}
+
+mbo_status mbo_diffuse(mbo_handle h, const void* A, void* A_tilde, void* stream) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
+  if ((rc = check_field_ptr(h, A_tilde, "A_tilde")) != MBO_OK) return rc;
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StatsPtrs none = stats_ptrs(h, false, false, -1.0);
+  h->w_valid_for = nullptr;
+  CK(row_pass(h, ROW_FWD, A, nullptr, none, s));
+  CK(middle_passes(h, AXIS_FGI, none, s));
+  CK(row_pass(h, ROW_INV_OUT, nullptr, A_tilde, none, s));
+  return MBO_OK;
+}
+
+mbo_status mbo_project(mbo_handle h, const void* A_tilde, void* B, int8_t* det_sign,
+                       void* stream) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A_tilde, "A_tilde")) != MBO_OK) return rc;
+  if ((rc = check_field_ptr(h, B, "B")) != MBO_OK) return rc;
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (B == h->w_valid_for) h->w_valid_for = nullptr;
+  CK(timed(h, MBO_PASS_PROJECT, s, [&]() {
+    if (h->dtype == MBO_F32)
+      return launch_project<float>(h->g, static_cast<const float*>(A_tilde),
+                                   static_cast<float*>(B), det_sign, h->cfg.fallback_sigma, s);
+    return launch_project<double>(h->g, static_cast<const double*>(A_tilde),
+                                  static_cast<double*>(B), det_sign, 0.0, s);
+  }));
+  return MBO_OK;
+}
+
+static mbo_status read_record(mbo_handle h, long long slot, mbo_stats* out) {
+  double v[5];
+  CK(cudaMemcpy(&v[0], h->hist.energy + slot, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&v[1], h->hist.maxdelta + slot, 8, cudaMemcpyDeviceToHost));
+  long long f[3];
+  CK(cudaMemcpy(&f[0], h->hist.flips + slot, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&f[1], h->hist.fallback + slot, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&f[2], h->hist.nonfinite + slot, 8, cudaMemcpyDeviceToHost));
+  out->energy = v[0];
+  out->max_delta = v[1];
+  out->det_flips = f[0];
+  out->fallback_points = f[1];
+  out->nonfinite = f[2];
+  return MBO_OK;
+}
+
+mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* stream) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool cont = (flags & MBO_STEP_CONTINUE) && h->w_valid_for == A;
+  if (!cont) CK(row_pass(h, ROW_FWD, A, nullptr, stats_ptrs(h, true, false, -1.0), s));
+  CK(step_passes(h, A, false, -1.0, s));
+  h->w_valid_for = A;
+  if (stats) {
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+    const long long slot = (h->h_st->step - 1) & (kRing - 1);
+    if ((rc = read_record(h, slot, stats)) != MBO_OK) return rc;
+    if (stats->nonfinite) return fail(h, MBO_ERR_NUMERIC, "%lld non-finite points", (long long)stats->nonfinite);
+  }
+  return MBO_OK;
+}
+
+mbo_status mbo_lyapunov(mbo_handle h, const void* A, double* E, void* stream) {
+  if (!h || !E) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StatsPtrs sp = stats_ptrs(h, true, false, -1.0);
+  CK(row_pass(h, ROW_FWD, A, nullptr, sp, s));
+  CK(middle_passes(h, AXIS_ENERGY, sp, s));
+  h->w_valid_for = (h->g.ndim == 2) ? A : nullptr;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+  *E = h->h_st->energy_last;
+  return MBO_OK;
+}
+
+mbo_status mbo_run_until_stationary(mbo_handle h, void* A, int max_steps, double tol,
+                                    int* steps_taken, int* stationary, double* energies,
+                                    double* max_deltas, int64_t* det_flips, mbo_stats* last,
+                                    void* stream) {
+  if (!h || max_steps < 0) return MBO_ERR_INVALID_ARG;
+  if (!A) return fail(h, MBO_ERR_INVALID_ARG, "A is NULL");
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fbytes = (size_t)h->g.C * (size_t)h->g.P * h->elem;
+  cudaPointerAttributes pa{};
+  CK(cudaPointerGetAttributes(&pa, A));
+  const bool host = pa.type == cudaMemoryTypeUnregistered || pa.type == cudaMemoryTypeHost;
+  void* dA = A;
+  if (host) {
+    if (!h->field) {
+      CK(cudaMalloc(&h->field, fbytes));
+      h->bytes_total += fbytes;
+    }
+    dA = h->field;
+    CK(cudaMemcpyAsync(dA, A, fbytes, cudaMemcpyHostToDevice, s));
+  } else {
+    mbo_status rc = check_field_ptr(h, A, "A");
+    if (rc != MBO_OK) return rc;
+  }
+  CK(cudaMemsetAsync(h->st, 0, sizeof(RunState), s));
+  CK(row_pass(h, ROW_FWD, dA, nullptr, stats_ptrs(h, true, false, -1.0), s));
+
+  const bool use_graph = h->cfg.use_graph != 0 && !h->prof;
+  // the first step is launched directly (kernel attributes get set outside
+  // capture); later steps replay a graph captured for this field and tol
+  if (use_graph && (h->g_ptr != dA || h->g_tol != tol)) invalidate_graph(h);
+  const int K = h->cfg.check_interval;
+  double* hh = static_cast<double*>(h->h_hist);
+  long long copied = 0;  // energies[0..copied) / deltas[0..copied) already copied out
+  long long nonfinite = 0;
+  int done = 0;
+  bool stopped = false;
+  auto harvest = [&](long long upto_step, bool final_energy) -> mbo_status {
+    CK(cudaMemcpy(h->h_hist, h->hist_mem, (size_t)kRing * 5 * sizeof(double),
+                  cudaMemcpyDeviceToHost));
+    const long long* fl = reinterpret_cast<const long long*>(hh + 2 * kRing);
+    const long long* nf = reinterpret_cast<const long long*>(hh + 4 * kRing);
+    for (long long i = copied; i < upto_step; ++i) {
+      const long long sl = i & (kRing - 1);
+      nonfinite += nf[sl];
+      if (energies) energies[i] = hh[sl];
+      if (max_deltas) max_deltas[i] = hh[kRing + sl];
+      if (det_flips) det_flips[i] = fl[sl];
+    }
+    if (final_energy && energies) energies[upto_step] = hh[upto_step & (kRing - 1)];
+    copied = upto_step;
+    return MBO_OK;
+  };
+  while (done < max_steps && !stopped) {
+    const int chunk = std::min(K, max_steps - done);
+    for (int i = 0; i < chunk; ++i) {
+      if (use_graph && done + i > 0) {
+        if (!h->gexec) {
+          cudaGraph_t graph = nullptr;
+          CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+          cudaError_t e = step_passes(h, dA, true, tol, h->cap);
+          cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+          if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, MBO_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(e),
+                        cudaGetErrorString(e2));
+          }
+          cudaError_t e3 = cudaGraphInstantiate(&h->gexec, graph, 0);
+          cudaGraphDestroy(graph);
+          if (e3 != cudaSuccess) return fail(h, MBO_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
+          h->g_ptr = dA;
+          h->g_tol = tol;
+        }
+        CK(cudaGraphLaunch(h->gexec, s));
+      } else {
+        CK(step_passes(h, dA, true, tol, s));
+      }
+    }
+    done += chunk;
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    stopped = h->h_st->stop != 0;
+    mbo_status rc = harvest(h->h_st->step, false);
+    if (rc != MBO_OK) return rc;
+    if (stopped) break;
+  }
+  const long long steps = h->h_st->step;
+  // energy of the final field: its forward x transform is in the workspace
+  CK(middle_passes(h, AXIS_ENERGY, stats_ptrs(h, true, false, -1.0), s));
+  CK(cudaStreamSynchronize(s));
+  mbo_status rc = harvest(steps, true);
+  if (rc != MBO_OK) return rc;
+  h->w_valid_for = (h->g.ndim == 2 && !host) ? dA : nullptr;
+  if (host) {
+    CK(cudaMemcpyAsync(A, dA, fbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (steps_taken) *steps_taken = (int)steps;
+  if (stationary) *stationary = stopped ? 1 : 0;
+  const long long* nf = reinterpret_cast<const long long*>(hh + 4 * kRing);
+  if (last) {
+    if (steps > 0) {
+      const long long sl = (steps - 1) & (kRing - 1);
+      const long long* fl = reinterpret_cast<const long long*>(hh + 2 * kRing);
+      const long long* fb = reinterpret_cast<const long long*>(hh + 3 * kRing);
+      last->energy = hh[sl];
+      last->max_delta = hh[kRing + sl];
+      last->det_flips = fl[sl];
+      last->fallback_points = fb[sl];
+      last->nonfinite = nf[sl];
+    } else {
+      memset(last, 0, sizeof(*last));
+      last->energy = hh[0];
+    }
+  }
+  if (nonfinite) return fail(h, MBO_ERR_NUMERIC, "%lld non-finite points during the run", nonfinite);
+  return MBO_OK;
+}
+
+mbo_status mbo_profile_enable(mbo_handle h, int enable) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(h->dev);
+  for (auto& p : h->pending) {
+    cudaEventSynchronize(p.b);
+    h->ev_free.push_back(p.a);
+    h->ev_free.push_back(p.b);
+  }
+  h->pending.clear();
+  for (int i = 0; i < MBO_PROFILE_PASSES; ++i) {
+    h->prof_ms[i] = 0;
+    h->prof_n[i] = 0;
+  }
+  h->prof = enable != 0;
+  return MBO_OK;
+}
+
+mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npass) {
+  if (!h || npass < 0) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(h->dev);
+  for (auto& p : h->pending) {
+    CK(cudaEventSynchronize(p.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p.a, p.b));
+    h->prof_ms[p.pass] += t;
+    h->prof_n[p.pass] += 1;
+    h->ev_free.push_back(p.a);
+    h->ev_free.push_back(p.b);
+  }
+  h->pending.clear();
+  for (int i = 0; i < npass && i < MBO_PROFILE_PASSES; ++i) {
+    if (ms) ms[i] = h->prof_ms[i];
+    if (launches) launches[i] = h->prof_n[i];
+  }
+  return MBO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,563 @@
+// Device building blocks of the GB300 MBO path: complex arithmetic, small
+// register DFTs, in-place mixed-radix transforms over sequences held in shared
+// memory, the per-point closest-orthogonal-matrix projections (Lemma 2.1 of
+// Osting & Wang, arXiv:1711.01365) and block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mbo_internal.h"
+
+namespace mbo {
+
+// ---------------------------------------------------------------------------
+// Complex helpers (interleaved re/im as float2 / double2)
+// ---------------------------------------------------------------------------
+template <typename R> struct VT;
+template <> struct VT<float> { using V = float2; };
+template <> struct VT<double> { using V = double2; };
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// multiply by DIR*i (DIR = -1: -i, DIR = +1: +i)
+template <int DIR, typename V> __device__ __forceinline__ V cmul_i(V a) {
+  return DIR < 0 ? V{a.y, -a.x} : V{-a.y, a.x};
+}
+
+// ---------------------------------------------------------------------------
+// Register DFTs: y_k = sum_l v_l exp(DIR 2 pi i l k / RAD), in place.
+// ---------------------------------------------------------------------------
+template <int DIR, typename V> __device__ __forceinline__ void dft2(V* v) {
+  V a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <int DIR, typename V> __device__ __forceinline__ void dft3(V* v) {
+  using R = decltype(v[0].x);
+  const R h = R(0.86602540378443864676);  // sqrt(3)/2
+  V s = cadd(v[1], v[2]);
+  V d = csub(v[1], v[2]);
+  V t1 = V{v[0].x - R(0.5) * s.x, v[0].y - R(0.5) * s.y};
+  V t2 = cmul_i<DIR>(V{h * d.x, h * d.y});
+  v[0] = cadd(v[0], s);
+  v[1] = cadd(t1, t2);
+  v[2] = csub(t1, t2);
+}
+
+template <int DIR, typename V> __device__ __forceinline__ void dft4(V* v) {
+  V s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  V s13 = cadd(v[1], v[3]), d13 = cmul_i<DIR>(csub(v[1], v[3]));
+  v[0] = cadd(s02, s13);
+  v[2] = csub(s02, s13);
+  v[1] = cadd(d02, d13);
+  v[3] = csub(d02, d13);
+}
+
+template <int DIR, typename V> __device__ __forceinline__ void dft8(V* v) {
+  using R = decltype(v[0].x);
+  const R c = R(0.70710678118654752440);
+  V e[4] = {v[0], v[2], v[4], v[6]};
+  V o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<DIR>(e);
+  dft4<DIR>(o);
+  // W8^k = exp(DIR 2 pi i k / 8)
+  o[1] = cmul(o[1], V{c, R(DIR) * c});
+  o[2] = cmul_i<DIR>(o[2]);
+  o[3] = cmul(o[3], V{-c, R(DIR) * c});
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <int DIR, typename V> __device__ __forceinline__ void dft16(V* v) {
+  using R = decltype(v[0].x);
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);
+  const R c2 = R(0.70710678118654752440);
+  V e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    e[k] = v[2 * k];
+    o[k] = v[2 * k + 1];
+  }
+  dft8<DIR>(e);
+  dft8<DIR>(o);
+  // W16^k = (cos(2 pi k/16), DIR sin(2 pi k/16)), k = 1..7
+  const R D = R(DIR);
+  o[1] = cmul(o[1], V{c1, D * s1});
+  o[2] = cmul(o[2], V{c2, D * c2});
+  o[3] = cmul(o[3], V{s1, D * c1});
+  o[4] = cmul_i<DIR>(o[4]);
+  o[5] = cmul(o[5], V{-s1, D * c1});
+  o[6] = cmul(o[6], V{-c2, D * c2});
+  o[7] = cmul(o[7], V{-c1, D * s1});
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 8] = csub(e[k], o[k]);
+  }
+}
+
+template <int DIR, int RAD, typename V> __device__ __forceinline__ void dft(V* v) {
+  if constexpr (RAD == 2) dft2<DIR>(v);
+  else if constexpr (RAD == 3) dft3<DIR>(v);
+  else if constexpr (RAD == 4) dft4<DIR>(v);
+  else if constexpr (RAD == 8) dft8<DIR>(v);
+  else dft16<DIR>(v);
+}
+
+// ---------------------------------------------------------------------------
+// Fast division (see FastDiv) and asynchronous global -> shared copies.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned fdiv(const FastDiv& d, unsigned x) {
+  return d.shift >= 0 ? (x >> d.shift) : __umulhi(x, d.mul);
+}
+
+// cp.async of one complex element (8 bytes for float2, 16 for double2); the
+// copy proceeds while the thread issues more; cp_async_wait_all() then a
+// barrier makes the data visible to the block.
+template <typename V> __device__ __forceinline__ void cp_async_elem(V* dst, const V* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(V) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layouts of M sequences of length N.
+//   RowLayout: sequence m at m*S, element p at p + p/16 (one pad slot per 16
+//              elements keeps short-span butterflies free of bank conflicts);
+//              butterflies map sequence-major (consecutive threads, consecutive j).
+//   ColLayout: element (m, p) at p*M + m (a tile of M = 2^ltx adjacent columns);
+//              butterflies map column-fastest.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int row_pad(int N) { return N + (N >> 4) + 1; }
+
+struct RowLayout {
+  static constexpr bool kColumns = false;
+  int S;
+  __device__ __forceinline__ int addr(int m, int p) const { return m * S + p + (p >> 4); }
+};
+struct ColLayout {
+  static constexpr bool kColumns = true;
+  int ltx;
+  __device__ __forceinline__ int addr(int m, int p) const { return (p << ltx) + m; }
+};
+
+// In-place mixed-radix transforms.  The forward transform is a decimation-in-
+// frequency network: natural-order input, spectrum left in digit-reversed
+// order.  The inverse is the matching decimation-in-time network (the
+// conjugate transpose of the forward stages, applied in reverse order): it
+// reads the digit-reversed spectrum and returns natural order.  Every
+// butterfly reads and writes the same RAD slots, so threads never hold more
+// than one butterfly and a stage needs only a barrier after it.  Multiplier
+// tables are permuted on the host to the digit-reversed positions.
+template <int DIR, int RAD, typename V, class L>
+__device__ __forceinline__ void radix_stage(V* s, const L& lay, int N, int M, const Stage& sd,
+                                            const V* __restrict__ tw) {
+  const int NR = N / RAD;
+  const int m = sd.m, lb = sd.lb;
+  const unsigned B = (unsigned)(NR * M);
+  const V* __restrict__ tws = tw + sd.tw;
+  for (unsigned u = threadIdx.x; u < B; u += blockDim.x) {
+    int seq, w;
+    if constexpr (L::kColumns) {
+      seq = (int)(u & ((1u << lay.ltx) - 1));
+      w = (int)(u >> lay.ltx);
+    } else {
+      seq = (int)fdiv(sd.dnr, u);
+      w = (int)u - seq * NR;
+    }
+    const int b = (int)fdiv(sd.dm, (unsigned)w);
+    const int n1 = w - b * m;
+    const int base = b * lb + n1;
+    V v[RAD];
+#pragma unroll
+    for (int j = 0; j < RAD; ++j) v[j] = s[lay.addr(seq, base + j * m)];
+    if (DIR < 0) {
+      dft<-1, RAD>(v);
+      if (m > 1) {
+        const V* t = tws + n1 * (RAD - 1);
+#pragma unroll
+        for (int j = 1; j < RAD; ++j) v[j] = cmul(v[j], __ldg(&t[j - 1]));
+      }
+    } else {
+      if (m > 1) {
+        const V* t = tws + n1 * (RAD - 1);
+#pragma unroll
+        for (int j = 1; j < RAD; ++j) {
+          V c = __ldg(&t[j - 1]);
+          c.y = -c.y;
+          v[j] = cmul(v[j], c);
+        }
+      }
+      dft<+1, RAD>(v);
+    }
+#pragma unroll
+    for (int j = 0; j < RAD; ++j) s[lay.addr(seq, base + j * m)] = v[j];
+  }
+  __syncthreads();
+}
+
+template <int DIR, typename V, class L>
+__device__ __forceinline__ void run_stage(V* s, const L& lay, int N, int M, const Stage& sd,
+                                          const V* __restrict__ tw) {
+  switch (sd.rad) {
+    case 16: radix_stage<DIR, 16>(s, lay, N, M, sd, tw); break;
+    case 8: radix_stage<DIR, 8>(s, lay, N, M, sd, tw); break;
+    case 4: radix_stage<DIR, 4>(s, lay, N, M, sd, tw); break;
+    case 3: radix_stage<DIR, 3>(s, lay, N, M, sd, tw); break;
+    default: radix_stage<DIR, 2>(s, lay, N, M, sd, tw); break;
+  }
+}
+
+// Forward transform (unnormalised, exp(-2 pi i k x / N)); caller synchronises before.
+template <typename V, class L>
+__device__ void fft_fwd(V* s, const L& lay, int N, int M, const Plan& pl, const V* __restrict__ tw) {
+  for (int st = 0; st < pl.nst; ++st) run_stage<-1>(s, lay, N, M, pl.st[st], tw);
+}
+
+// Inverse transform (unnormalised, exp(+2 pi i k x / N)) of a digit-reversed spectrum.
+template <typename V, class L>
+__device__ void fft_inv(V* s, const L& lay, int N, int M, const Plan& pl, const V* __restrict__ tw) {
+  for (int st = pl.nst - 1; st >= 0; --st) run_stage<+1>(s, lay, N, M, pl.st[st], tw);
+}
+
+// ---------------------------------------------------------------------------
+// Closest orthogonal matrix (Lemma 2.1).  Input m and output b are row-major
+// n x n.  Returns the class sign s = +1 if det m >= 0 else -1 (det b = s) and
+// the smallest singular value of m in smin.
+// ---------------------------------------------------------------------------
+template <typename R> struct JacobiPrec;
+template <> struct JacobiPrec<float> {
+  static constexpr float tol = 1e-6f;
+  static constexpr int sweeps = 6;
+};
+template <> struct JacobiPrec<double> {
+  static constexpr double tol = 2e-15;
+  static constexpr int sweeps = 12;
+};
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+
+// n = 1: nearest of {+1, -1}.
+template <typename R> __device__ __forceinline__ R polar1(const R* m, R* b, R& smin) {
+  const R s = (m[0] >= R(0)) ? R(1) : R(-1);
+  b[0] = s;
+  smin = fabs(m[0]);
+  return s;
+}
+
+// n = 2, closed form.  With p = a+d, q = c-b, r = a-d, t = b+c for
+// A = [[a,b],[c,d]]: sigma_{1,2} = (sqrt(p^2+q^2) +- sqrt(r^2+t^2)) / 2 and
+// det A = ((p^2+q^2) - (r^2+t^2)) / 4.  The nearest rotation is the
+// normalised [[p,-q],[q,p]], the nearest reflection the normalised
+// [[r,t],[t,-r]]; the class follows the sign of det A.
+template <typename R> __device__ __forceinline__ R polar2(const R* m, R* b, R& smin) {
+  const R p = m[0] + m[3], q = m[2] - m[1], r = m[0] - m[3], t = m[1] + m[2];
+  const R rho2 = p * p + q * q, sig2 = r * r + t * t;
+  const R rho = sqrt(rho2), sig = sqrt(sig2);
+  smin = R(0.5) * fabs(rho - sig);
+  if (rho2 >= sig2) {
+    if (rho2 > R(0)) {
+      const R inv = R(1) / rho;
+      b[0] = p * inv; b[1] = -q * inv; b[2] = q * inv; b[3] = p * inv;
+    } else {
+      b[0] = R(1); b[1] = R(0); b[2] = R(0); b[3] = R(1);
+    }
+    return R(1);
+  }
+  const R inv = R(1) / sig;
+  b[0] = r * inv; b[1] = t * inv; b[2] = t * inv; b[3] = -r * inv;
+  return R(-1);
+}
+
+template <typename R> __device__ __forceinline__ R dot3(const R* a, const R* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// One-sided Jacobi rotation of columns P and Q of A (and of V).
+template <int P, int Q, typename R>
+__device__ __forceinline__ void jacobi_pair(R (&a)[3][3], R (&v)[3][3], bool& rot) {
+  const R al = dot3(a[P], a[P]);
+  const R be = dot3(a[Q], a[Q]);
+  const R ga = dot3(a[P], a[Q]);
+  if (fabs(ga) > JacobiPrec<R>::tol * sqrt(al * be)) {
+    const R ze = (be - al) / (R(2) * ga);
+    const R t = copysign(R(1), ze) / (fabs(ze) + sqrt(R(1) + ze * ze));
+    const R c = rsqrt_(R(1) + t * t);
+    const R s = c * t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R ap = a[P][i], aq = a[Q][i];
+      a[P][i] = c * ap - s * aq;
+      a[Q][i] = s * ap + c * aq;
+      const R vp = v[P][i], vq = v[Q][i];
+      v[P][i] = c * vp - s * vq;
+      v[Q][i] = s * vp + c * vq;
+    }
+    rot = true;
+  }
+}
+
+template <typename R> __device__ __forceinline__ void cross3(const R* a, const R* b, R* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Unit vector orthogonal to the unit vector u (Gram-Schmidt of the axis least
+// aligned with u).
+template <typename R> __device__ __forceinline__ void any_orthogonal(const R* u, R* w) {
+  int k = 0;
+  if (fabs(u[1]) < fabs(u[k])) k = 1;
+  if (fabs(u[2]) < fabs(u[k])) k = 2;
+  R e[3] = {R(0), R(0), R(0)};
+  e[k] = R(1);
+  const R d = u[k];
+  R x[3] = {e[0] - d * u[0], e[1] - d * u[1], e[2] - d * u[2]};
+  const R inv = rsqrt_(dot3(x, x));
+  w[0] = x[0] * inv; w[1] = x[1] * inv; w[2] = x[2] * inv;
+}
+
+// n = 3: one-sided (Hestenes) Jacobi on the columns of m, then
+// U = [u_big, u_mid, +-u_big x u_mid] (orthonormal by construction, with the
+// smallest-singular-value column oriented so that det(U V^t) = sign det m),
+// V re-orthonormalised, b = U V^t.
+template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& smin) {
+  const R det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                m[2] * (m[3] * m[7] - m[4] * m[6]);
+  const R sg = (det >= R(0)) ? R(1) : R(-1);
+  R a[3][3] = {{m[0], m[3], m[6]}, {m[1], m[4], m[7]}, {m[2], m[5], m[8]}};  // a[j] = column j
+  R v[3][3] = {{R(1), R(0), R(0)}, {R(0), R(1), R(0)}, {R(0), R(0), R(1)}};
+#pragma unroll 1
+  for (int sw = 0; sw < JacobiPrec<R>::sweeps; ++sw) {
+    bool rot = false;
+    jacobi_pair<0, 1>(a, v, rot);
+    jacobi_pair<0, 2>(a, v, rot);
+    jacobi_pair<1, 2>(a, v, rot);
+    if (!rot) break;
+  }
+  const R n0 = dot3(a[0], a[0]), n1 = dot3(a[1], a[1]), n2 = dot3(a[2], a[2]);
+  // order the columns: ib (largest), im, is (smallest)
+  int ib = 0, is = 0;
+  if (n1 > n0) ib = 1;
+  if (n2 > (ib == 0 ? n0 : n1)) ib = 2;
+  if (n1 < n0) is = 1;
+  if (n2 < (is == 0 ? n0 : n1)) is = 2;
+  if (is == ib) is = (ib + 1) % 3;  // all equal
+  const int im = 3 - ib - is;
+  const R nn[3] = {n0, n1, n2};
+  smin = sqrt(nn[is]);
+  if (!(nn[ib] > R(0))) {  // m = 0 (or not finite): identity
+#pragma unroll
+    for (int i = 0; i < 9; ++i) b[i] = (i % 4 == 0) ? R(1) : R(0);
+    return (nn[ib] == R(0)) ? R(1) : sg;
+  }
+  R U[3][3];  // U[j] = column j
+  {
+    const R inv = rsqrt_(nn[ib]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) U[ib][i] = a[ib][i] * inv;
+    const R d = dot3(U[ib], a[im]);
+    R w[3] = {a[im][0] - d * U[ib][0], a[im][1] - d * U[ib][1], a[im][2] - d * U[ib][2]};
+    const R ww = dot3(w, w);
+    if (ww > R(0) && ww > nn[ib] * R(1e-30)) {
+      const R iw = rsqrt_(ww);
+      U[im][0] = w[0] * iw; U[im][1] = w[1] * iw; U[im][2] = w[2] * iw;
+    } else {
+      any_orthogonal(U[ib], U[im]);
+    }
+    // cyclic (ib, im, is) is an even permutation of (0, 1, 2)
+    const R perm = (im == (ib + 1) % 3) ? R(1) : R(-1);
+    R c[3];
+    cross3(U[ib], U[im], c);
+    const R f = perm * sg;
+    U[is][0] = f * c[0]; U[is][1] = f * c[1]; U[is][2] = f * c[2];
+  }
+  // re-orthonormalise V (a product of rotations: keep det V = +1)
+  {
+    const R i0 = rsqrt_(dot3(v[0], v[0]));
+    v[0][0] *= i0; v[0][1] *= i0; v[0][2] *= i0;
+    const R d = dot3(v[0], v[1]);
+    v[1][0] -= d * v[0][0]; v[1][1] -= d * v[0][1]; v[1][2] -= d * v[0][2];
+    const R i1 = rsqrt_(dot3(v[1], v[1]));
+    v[1][0] *= i1; v[1][1] *= i1; v[1][2] *= i1;
+    cross3(v[0], v[1], v[2]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[i * 3 + k] = U[0][i] * v[0][k] + U[1][i] * v[1][k] + U[2][i] * v[2][k];
+  return sg;
+}
+
+// n = 3, scaled Newton iteration for the polar factor (Higham 1986):
+//   X <- (zeta X + X^{-t} / zeta) / 2,  zeta = (|X^{-1}|_F / |X|_F)^{1/2},
+// with X^{-t} = cof(X) / det(X).  Each iterate keeps the singular vectors of
+// m (the singular values s map to (zeta s + 1/(zeta s)) / 2), so the limit is
+// U V^t of Lemma 2.1 and det X keeps the sign of det m.  Stops when an update
+// moves X by less than sqrt(tol2) (quadratic convergence) or after ITMAX
+// iterations.  est receives |det m| / |cof m|_F, which lies in
+// [sigma_min / sqrt(3), sigma_min]; callers route points with small est (and
+// exactly singular ones, where the iteration is undefined) elsewhere.
+template <int ITMAX, typename R>
+__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R tol2) {
+  R X[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X[k] = m[k];
+  R sg = R(1);
+#pragma unroll 1
+  for (int it = 0; it < ITMAX; ++it) {
+    R C[9];
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    const R det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    R nx = R(0), nc = R(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      nx += X[k] * X[k];
+      nc += C[k] * C[k];
+    }
+    if (it == 0) {
+      sg = (det >= R(0)) ? R(1) : R(-1);
+      est = fabs(det) * rsqrt_(nc);
+      if (!(est > R(0))) break;  // singular or not finite: caller's fallback
+    }
+    const R zeta = sqrt(sqrt(nc / (det * det * nx)));
+    const R a = R(0.5) * zeta;
+    const R c = R(0.5) / (zeta * det);
+    R diff = R(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const R xn = a * X[k] + c * C[k];
+      diff += (xn - X[k]) * (xn - X[k]);
+      X[k] = xn;
+    }
+    if (diff < tol2) break;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) b[k] = X[k];
+  return sg;
+}
+
+template <int NM, typename R> __device__ __forceinline__ R polar(const R* m, R* b, R& smin) {
+  if constexpr (NM == 1) return polar1(m, b, smin);
+  else if constexpr (NM == 2) return polar2(m, b, smin);
+  else return polar3(m, b, smin);
+}
+
+// FP64 projection used by the FP64 path and by the FP32 path's
+// re-projection: Newton, and the one-sided Jacobi construction for matrices
+// that are singular to working precision (rank-deficient ties included).
+template <int NM> __device__ __forceinline__ double polar_f64(const double* m, double* b, double& smin) {
+  if constexpr (NM == 3) {
+    double nx = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
+    double est = 0.0;
+    const double sg = polar3_newton<16>(m, b, est, 1e-22);
+    smin = est;
+    if (est > 1e-12 * sqrt(nx)) return sg;
+    return polar3(m, b, smin);
+  } else {
+    return polar<NM>(m, b, smin);
+  }
+}
+
+// Sign of det of an (orthogonal) matrix: +1 / -1.
+template <int NM, typename R> __device__ __forceinline__ R det_sign(const R* m) {
+  R d;
+  if constexpr (NM == 1) d = m[0];
+  else if constexpr (NM == 2) d = m[0] * m[3] - m[1] * m[2];
+  else
+    d = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+        m[2] * (m[3] * m[7] - m[4] * m[6]);
+  return d >= R(0) ? R(1) : R(-1);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum in a fixed order (deterministic).  red needs 32 slots.
+template <typename T> __device__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T r = T(0);
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = (l < nw) ? red[l] : T(0);
+    r = warp_sum(r);
+  }
+  return r;  // valid in thread 0
+}
+template <typename T> __device__ T block_max(T v, T* red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T r = T(0);
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = (l < nw) ? red[l] : T(0);
+    r = warp_max(r);
+  }
+  return r;
+}
+
+// Last-block-done pattern: returns true in exactly one block (the last to
+// arrive), after all blocks' earlier global writes are visible to it.
+__device__ __forceinline__ bool last_block_arrives(unsigned int* counter, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *s_flag = (prev == gridDim.x * gridDim.y * gridDim.z - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *s_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Fixed-order sum of a partial array by one block (deterministic).
+__device__ __forceinline__ double sum_partials(const double* p, int count, double* red) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += __ldcg(&p[i]);
+  return block_sum(acc, red);
+}
+
+}  // namespace mbo

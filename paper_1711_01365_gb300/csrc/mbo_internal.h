@@ -1,0 +1,112 @@
+// Internal types shared by the host API (mbo_api.cu) and the kernels
+// (mbo_kernels.cuh).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mbo {
+
+constexpr int kMaxStages = 8;
+constexpr int kRing = 1024;      // step-record ring (power of two)
+constexpr int kMaxThreads = 512; // row and axis kernels are launched with <= this many threads
+constexpr int kFallbackCap = 64; // per-row FP64 re-projection slots (FP32 path)
+
+// Division of x < 65536 by a fixed d < 65536: a shift when d is a power of
+// two (shift >= 0), else the high word of x * ceil(2^32 / d), which is exact
+// in that range.
+struct FastDiv {
+  unsigned mul;
+  int shift;
+};
+
+// One forward stage: radix rad on blocks of length lb = N / (rad_0 ... rad_{st-1});
+// a butterfly (block b, offset n1 < m = lb / rad) owns positions b*lb + n1 + m*j.
+// tw is the offset of the stage's twiddles exp(-2 pi i n1 j / lb), stored
+// [n1][j - 1], in the axis twiddle table (unused when m == 1).
+struct Stage {
+  int rad, lb, m, tw;
+  FastDiv dm;   // division by m
+  FastDiv dnr;  // division by N / rad
+};
+
+// Radix plan of one axis: forward stages applied in order, product = N.
+struct Plan {
+  int nst;
+  Stage st[kMaxStages];
+};
+
+// Device-resident state of a run.  Accumulators are reset by the finaliser
+// of the projection pass at the end of every step.
+struct RunState {
+  unsigned long long maxdelta_bits;  // bit pattern of a non-negative double (atomicMax)
+  unsigned long long flips;
+  unsigned long long fallback;
+  unsigned long long nonfinite;
+  double defect;       // sum_x (n - |A(x)|_F^2) of the field whose spectrum is in the workspace
+  double energy_last;  // last energy written by a transform pass
+  long long step;      // steps completed in this run
+  int stop;            // 1 once a stationary step was seen (run loop only)
+  unsigned int done_axis;  // last-block counters
+  unsigned int done_row;
+  unsigned int pad_;
+};
+
+// Step-record ring, indexed by step & (kRing - 1).
+struct Hist {
+  double* energy;
+  double* maxdelta;
+  long long* flips;
+  long long* fallback;
+  long long* nonfinite;
+};
+
+// Geometry of a field.  dims are (nz, ny, nx); nz = 1 in 2-D.
+struct Geom {
+  int ndim;
+  int nx, ny, nz;
+  long long P;
+  int n, C, Q;
+  double tau;
+};
+
+// Per-axis tables in the element type R (0 = x, 1 = y, 2 = z).
+template <typename R> struct Tables {
+  const void* tw[3];   // per-stage twiddles of each axis (see Stage::tw)
+  const R* g[3];       // exp(-4 pi^2 tau k^2), k the signed frequency held at each
+                       // digit-reversed spectrum position of the forward transform
+  const R* om[3];      // 1 - g at the same positions (computed as -expm1)
+  Plan plan[3];
+  R inv_p;             // 1 / P, folded into the multiplier
+};
+
+// Pass modes of the strided-axis kernel.
+enum AxisMode { AXIS_FWD = 0, AXIS_INV = 1, AXIS_FGI = 2, AXIS_ENERGY = 3 };
+// Modes of the row (x-axis) kernel.
+enum RowMode { ROW_FWD = 0, ROW_INV_OUT = 1, ROW_INV_PROJECT_FWD = 2 };
+
+struct StatsPtrs {
+  RunState* st;
+  Hist hist;
+  double* part;        // per-block partial sums
+  int respect_stop;    // 1: return at once if st->stop is set
+  int do_stats;        // 1: accumulate and finalise statistics
+  double tol;          // stationarity tolerance (< 0: never stop)
+};
+
+// Launchers (defined per element type in k_f32.cu / k_f64.cu).
+template <typename R>
+cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R* A_in, R* A_out,
+                       void* W, const StatsPtrs& sp, double fallback_sigma, int threads,
+                       cudaStream_t s);
+template <typename R>
+cudaError_t launch_axis(AxisMode mode, int axis, const Geom& g, const Tables<R>& t, void* W,
+                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s);
+template <typename R>
+cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
+                           double fallback_sigma, cudaStream_t s);
+
+// Shared memory bytes of the row kernel for a geometry.
+size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback);
+size_t axis_smem_bytes(int len, int tx, size_t elem_bytes);
+
+}  // namespace mbo

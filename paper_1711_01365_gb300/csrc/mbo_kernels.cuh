@@ -1,0 +1,469 @@
+// Kernels of the flat-torus MBO step (Algorithm 1 of Osting & Wang,
+// arXiv:1711.01365) and their launchers.  Instantiated per element type in
+// k_f32.cu and k_f64.cu.
+//
+// Data layout in HBM
+//   field A      planar: channel c = i*n + j, P values each, row-major (z, y, x)
+//   workspace W  Q = ceil(n*n/2) complex planes of P points; plane q packs
+//                channels 2q (real part) and 2q+1 (imaginary part).  Because
+//                the heat multiplier is real and even, the packed transform of
+//                two real channels diffuses both at once (Sec. 5.1 applies the
+//                same convolution "entry by entry").
+//
+// Transforms along each axis are in place in shared memory: forward DIF
+// (spectrum left digit-reversed along that axis), inverse DIT.
+// Passes of one step (steady state, 2-D):
+//   k_axis<FGI>   along y: forward DFT, x g(k)/P (Sec. 5.1), energy partials
+//                 (Eq. 4.1, Parseval form), inverse DFT
+//   k_row<INV_PROJECT_FWD> along x: inverse DFT, per-point polar factor
+//                 (Lemma 2.1), step statistics, then the forward x-DFT of the
+//                 new field for the next step
+// 3-D adds k_axis<FWD> and k_axis<INV> along y around the z pass.
+#pragma once
+#include "mbo_dev.cuh"
+
+namespace mbo {
+
+// Statistics of the points a thread projected.
+template <typename R> struct PointStats {
+  R maxd = R(0);
+  R defect = R(0);
+  int flips = 0;
+  int nonfinite = 0;
+  int fallback = 0;
+};
+
+// Project one point in the element type R.  Returns false when the point
+// must be re-projected in FP64 instead: FP32 points whose smallest singular
+// value is below fb (the configured threshold), and FP32 points singular to
+// single precision (always).  FP64 elements are always projected here.
+template <int NM, typename R>
+__device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
+  if constexpr (sizeof(R) == 8) {
+    double sm;
+    sg = polar_f64<NM>(m, b, sm);
+    return true;
+  } else if constexpr (NM == 3) {
+    float nx = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
+    float est = 0.f;
+    sg = polar3_newton<10>(m, b, est, 1e-10f);
+    return !(est < fb) && est > 1e-6f * sqrtf(nx);
+  } else {
+    float sm;
+    sg = polar<NM>(m, b, sm);
+    return !(NM >= 2 && sm < fb);
+  }
+}
+
+// FP64 projection of an element-type point (the re-projection path).
+template <int NM, typename R>
+__device__ __forceinline__ R project_point_f64(const R* m, R* b) {
+  constexpr int C = NM * NM;
+  double md[C], bd[C], sd;
+#pragma unroll
+  for (int c = 0; c < C; ++c) md[c] = (double)m[c];
+  const double sg = polar_f64<NM>(md, bd, sd);
+#pragma unroll
+  for (int c = 0; c < C; ++c) b[c] = (R)bd[c];
+  return (R)sg;
+}
+
+// Record a projected point: compare with the old field, write the new value
+// to global memory and (packed) to the shared row.
+template <int NM, typename R, typename V>
+__device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, long long off, int x,
+                                             const R* old, const R* b, R sg, V* s,
+                                             const RowLayout& lay, PointStats<R>& ps) {
+  constexpr int C = NM * NM, Q = (C + 1) / 2;
+  R d = R(0), nb = R(0);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    d = fmax(d, fabs(b[c] - old[c]));
+    nb += b[c] * b[c];
+  }
+  ps.maxd = fmax(ps.maxd, d);
+  ps.flips += (det_sign<NM>(old) != sg) ? 1 : 0;
+  ps.defect += R(NM) - nb;
+#pragma unroll
+  for (int c = 0; c < C; ++c) A[c * P + off + x] = b[c];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) s[lay.addr(q, x)] = V{b[2 * q], (2 * q + 1 < C) ? b[2 * q + 1] : R(0)};
+}
+
+template <typename R, int NM, int MODE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W, StatsPtrs sp,
+      R fb_sigma) {
+  using V = typename VT<R>::V;
+  constexpr int C = NM * NM, Q = (C + 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double redd[32];
+  __shared__ int redi[32];
+  __shared__ int s_flag, s_nfb;
+  if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
+
+  V* s = reinterpret_cast<V*>(smem_raw);
+  const int nx = g.nx;
+  const int S = row_pad(nx);
+  const RowLayout lay{S};
+  const long long P = g.P;
+  const long long off = (long long)blockIdx.x * nx;
+  const int T = blockDim.x, tid = threadIdx.x;
+  const V* tw = static_cast<const V*>(t.tw[0]);
+  const bool is_f32 = sizeof(R) == 4;
+
+  if (MODE == ROW_FWD) {
+    R defect = R(0);
+    for (int x = tid; x < nx; x += T) {
+      R sq = R(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const R re = Ain[(2 * q) * P + off + x];
+        const R im = (2 * q + 1 < C) ? Ain[(2 * q + 1) * P + off + x] : R(0);
+        s[lay.addr(q, x)] = V{re, im};
+        sq += re * re + im * im;
+      }
+      defect += R(NM) - sq;
+    }
+    __syncthreads();
+    fft_fwd(s, lay, nx, Q, t.plan[0], tw);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      for (int x = tid; x < nx; x += T) W[q * P + off + x] = s[lay.addr(q, x)];
+    if (sp.do_stats) {
+      const double tot = block_sum((double)defect, redd);
+      if (tid == 0) sp.part[blockIdx.x] = tot;
+      if (last_block_arrives(&sp.st->done_row, &s_flag)) {
+        const double all = sum_partials(sp.part, gridDim.x, redd);
+        if (tid == 0) {
+          sp.st->defect = all;
+          sp.st->done_row = 0;
+        }
+      }
+    }
+    return;
+  }
+
+  // inverse modes: load the spectrum rows (asynchronous copies)
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    for (int x = tid; x < nx; x += T) cp_async_elem(&s[lay.addr(q, x)], &W[q * P + off + x]);
+  cp_async_wait_all();
+  __syncthreads();
+  fft_inv(s, lay, nx, Q, t.plan[0], tw);
+
+  if (MODE == ROW_INV_OUT) {
+    for (int x = tid; x < nx; x += T) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const V z = s[lay.addr(q, x)];
+        A[(2 * q) * P + off + x] = z.x;
+        if (2 * q + 1 < C) A[(2 * q + 1) * P + off + x] = z.y;
+      }
+    }
+    return;
+  }
+
+  // ROW_INV_PROJECT_FWD
+  float* fbM = reinterpret_cast<float*>(s + Q * S);
+  int* fbX = reinterpret_cast<int*>(fbM + kFallbackCap * C);
+  if (tid == 0) s_nfb = 0;
+  __syncthreads();
+  PointStats<R> ps;
+  for (int x = tid; x < nx; x += T) {
+    R old[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) old[c] = A[c * P + off + x];
+    R m[C];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const V z = s[lay.addr(q, x)];
+      m[2 * q] = z.x;
+      if (2 * q + 1 < C) m[2 * q + 1] = z.y;
+    }
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+    ps.nonfinite += fin ? 0 : 1;
+    R b[C];
+    R sg;
+    if (!project_point<NM>(m, b, sg, fb_sigma) && fin) {
+      const int slot = atomicAdd(&s_nfb, 1);
+      if (slot < kFallbackCap) {
+        fbX[slot] = x;
+#pragma unroll
+        for (int c = 0; c < C; ++c) fbM[slot * C + c] = (float)m[c];
+        continue;
+      }
+      sg = project_point_f64<NM>(m, b);
+      ps.fallback += 1;
+    }
+    finish_point<NM>(A, P, off, x, old, b, sg, s, lay, ps);
+  }
+  if (is_f32 && NM >= 2) {
+    __syncthreads();
+    const int nf = min(s_nfb, kFallbackCap);
+    for (int k = tid; k < nf; k += T) {
+      const int x = fbX[k];
+      R m[C], b[C], old[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        m[c] = (R)fbM[k * C + c];
+        old[c] = A[c * P + off + x];
+      }
+      const R sg = project_point_f64<NM>(m, b);
+      ps.fallback += 1;
+      finish_point<NM>(A, P, off, x, old, b, sg, s, lay, ps);
+    }
+  }
+  __syncthreads();
+  fft_fwd(s, lay, nx, Q, t.plan[0], tw);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    for (int x = tid; x < nx; x += T) W[q * P + off + x] = s[lay.addr(q, x)];
+
+  if (!sp.do_stats) return;
+  const double dsum = block_sum((double)ps.defect, redd);
+  const double mx = block_max((double)ps.maxd, redd);
+  const int fl = block_sum(ps.flips, redi);
+  const int nfin = block_sum(ps.nonfinite, redi);
+  const int nfb = block_sum(ps.fallback, redi);
+  if (tid == 0) {
+    sp.part[blockIdx.x] = dsum;
+    atomicMax(&sp.st->maxdelta_bits, (unsigned long long)__double_as_longlong(mx));
+    if (fl) atomicAdd(&sp.st->flips, (unsigned long long)fl);
+    if (nfin) atomicAdd(&sp.st->nonfinite, (unsigned long long)nfin);
+    if (nfb) atomicAdd(&sp.st->fallback, (unsigned long long)nfb);
+  }
+  if (last_block_arrives(&sp.st->done_row, &s_flag)) {
+    const double all = sum_partials(sp.part, gridDim.x, redd);
+    if (tid == 0) {
+      RunState* st = sp.st;
+      st->defect = all;
+      const long long slot = st->step & (kRing - 1);
+      const double md = __longlong_as_double((long long)atomicAdd(&st->maxdelta_bits, 0ull));
+      const unsigned long long f = atomicAdd(&st->flips, 0ull);
+      const unsigned long long nb = atomicAdd(&st->fallback, 0ull);
+      const unsigned long long nn = atomicAdd(&st->nonfinite, 0ull);
+      sp.hist.maxdelta[slot] = md;
+      sp.hist.flips[slot] = (long long)f;
+      sp.hist.fallback[slot] = (long long)nb;
+      sp.hist.nonfinite[slot] = (long long)nn;
+      if (sp.tol >= 0.0 && f == 0 && md <= sp.tol) st->stop = 1;
+      st->maxdelta_bits = 0;
+      st->flips = 0;
+      st->fallback = 0;
+      st->nonfinite = 0;
+      st->step += 1;
+      st->done_row = 0;
+    }
+  }
+}
+
+// Strided-axis pass (y in 2-D; y and z in 3-D).  One block owns a tile of tx
+// adjacent x-columns of one complex plane along the whole axis.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int ltx) {
+  using V = typename VT<R>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double redd[32];
+  __shared__ int s_flag;
+  if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
+
+  V* s = reinterpret_cast<V*>(smem_raw);
+  const int tx = 1 << ltx;
+  const int L = (axis == 1) ? g.ny : g.nz;
+  const long long es = (axis == 1) ? (long long)g.nx : (long long)g.nx * g.ny;
+  const int xt = g.nx >> ltx;
+  const int nouter = (axis == 1) ? g.nz : g.ny;
+  const long long ostride = (axis == 1) ? (long long)g.nx * g.ny : (long long)g.nx;
+  const int per_plane = nouter * xt;
+  const int tile = blockIdx.x;
+  const int q = tile / per_plane;
+  const int rem = tile - q * per_plane;
+  const int o = rem / xt;
+  const int x0 = (rem - o * xt) << ltx;
+  V* base = W + (long long)q * g.P + (long long)o * ostride + x0;
+  const ColLayout lay{ltx};
+  const int T = blockDim.x, tid = threadIdx.x;
+  const V* tw = static_cast<const V*>(t.tw[axis]);
+
+  // Thread tid always owns column m = tid % tx of the tile (T is a multiple of
+  // tx); it walks the axis with a fixed pointer stride.
+  const int mcol = tid & (tx - 1);
+  const int p0 = tid >> ltx, dp = T >> ltx;
+  const long long gstep = (long long)dp * es;
+  {
+    const V* src = base + mcol + (long long)p0 * es;
+    for (int p = p0; p < L; p += dp, src += gstep) cp_async_elem(&s[(p << ltx) + mcol], src);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (MODE != AXIS_INV) fft_fwd(s, lay, L, tx, t.plan[axis], tw);
+  R acc = R(0);
+  if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
+    // the last axis applies g(k) = g_x g_y (g_z); in 3-D the y frequency is
+    // the outer index o of this tile (the y pass ran before).
+    R go = R(1), omo = R(0);
+    if (g.ndim == 3) {
+      go = t.g[1][o];
+      omo = t.om[1][o];
+    }
+    const R* gL = t.g[axis];
+    const R* omL = t.om[axis];
+    const int x = x0 + mcol;
+    const R gxx = t.g[0][x];
+    const R omx = t.om[0][x];
+    const R fo = gxx * go * t.inv_p;
+    const R omo2 = gxx * go;
+    for (int p = p0; p < L; p += dp) {
+      const int e = (p << ltx) + mcol;
+      const R omv = omx + gxx * omo + omo2 * omL[p];  // 1 - g without cancellation
+      V z = s[e];
+      acc += omv * (z.x * z.x + z.y * z.y);
+      if (MODE == AXIS_FGI) {
+        const R f = fo * gL[p];
+        s[e] = V{z.x * f, z.y * f};
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE == AXIS_FGI || MODE == AXIS_INV) fft_inv(s, lay, L, tx, t.plan[axis], tw);
+  if (MODE != AXIS_ENERGY) {
+    V* dst = base + mcol + (long long)p0 * es;
+    for (int p = p0; p < L; p += dp, dst += gstep) *dst = s[(p << ltx) + mcol];
+  }
+  if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
+    const double tot = block_sum((double)acc, redd);
+    if (tid == 0) sp.part[blockIdx.x] = tot;
+    if (last_block_arrives(&sp.st->done_axis, &s_flag)) {
+      const double all = sum_partials(sp.part, gridDim.x, redd);
+      if (tid == 0) {
+        RunState* st = sp.st;
+        const double Pd = (double)g.P;
+        const double E_tau = (all / Pd + st->defect) / (Pd * g.tau);
+        st->energy_last = E_tau;
+        sp.hist.energy[st->step & (kRing - 1)] = E_tau;
+        st->done_axis = 0;
+      }
+    }
+  }
+}
+
+// Pointwise projection of a diffused field (the unfused projection step).
+template <typename R, int NM>
+__global__ void __launch_bounds__(256)
+k_project(long long P, const R* At, R* B, int8_t* ds, R fb_sigma) {
+  constexpr int C = NM * NM;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < P;
+       x += (long long)gridDim.x * blockDim.x) {
+    R m[C], b[C], sg;
+#pragma unroll
+    for (int c = 0; c < C; ++c) m[c] = At[c * P + x];
+    if (!project_point<NM>(m, b, sg, fb_sigma)) sg = project_point_f64<NM>(m, b);
+#pragma unroll
+    for (int c = 0; c < C; ++c) B[c * P + x] = b[c];
+    if (ds) ds[x] = (sg > R(0)) ? 1 : -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+// Raise a kernel's dynamic shared-memory limit once (per process) to the
+// largest size it was launched with; launches inside graph capture then make
+// no attribute call.
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes, size_t& done) {
+  if (bytes <= 48 * 1024 || bytes <= done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = bytes;
+  return e;
+}
+
+template <typename R, int NM, int MODE>
+static cudaError_t launch_row_nm(const Geom& g, const Tables<R>& t, const R* Ain, R* A, void* W,
+                                 const StatsPtrs& sp, R fb, int threads, cudaStream_t s) {
+  auto k = k_row<R, NM, MODE>;
+  static size_t done = 0;
+  const size_t smem = row_smem_bytes(g, sizeof(R), MODE == ROW_INV_PROJECT_FWD);
+  cudaError_t e = set_smem(k, smem, done);
+  if (e != cudaSuccess) return e;
+  const int rows = g.nz * g.ny;
+  k<<<rows, threads, smem, s>>>(g, t, Ain, A, static_cast<typename VT<R>::V*>(W), sp, fb);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R* A_in, R* A_out,
+                       void* W, const StatsPtrs& sp, double fallback_sigma, int threads,
+                       cudaStream_t s) {
+  const R fb = (R)fallback_sigma;
+#define MBO_ROW_CASE(NM)                                                                   \
+  if (g.n == NM) {                                                                         \
+    if (mode == ROW_FWD)                                                                   \
+      return launch_row_nm<R, NM, ROW_FWD>(g, t, A_in, A_out, W, sp, fb, threads, s);      \
+    if (mode == ROW_INV_OUT)                                                               \
+      return launch_row_nm<R, NM, ROW_INV_OUT>(g, t, A_in, A_out, W, sp, fb, threads, s);  \
+    return launch_row_nm<R, NM, ROW_INV_PROJECT_FWD>(g, t, A_in, A_out, W, sp, fb, threads, \
+                                                     s);                                   \
+  }
+  MBO_ROW_CASE(1)
+  MBO_ROW_CASE(2)
+  MBO_ROW_CASE(3)
+#undef MBO_ROW_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, int MODE>
+static cudaError_t launch_axis_m(const Geom& g, const Tables<R>& t, void* W, const StatsPtrs& sp,
+                                 int axis, int tx, int threads, cudaStream_t s) {
+  auto k = k_axis<R, MODE>;
+  static size_t done = 0;
+  const int L = axis == 1 ? g.ny : g.nz;
+  const size_t smem = axis_smem_bytes(L, tx, sizeof(R));
+  cudaError_t e = set_smem(k, smem, done);
+  if (e != cudaSuccess) return e;
+  int ltx = 0;
+  while ((1 << ltx) < tx) ++ltx;
+  const int nouter = axis == 1 ? g.nz : g.ny;
+  const int tiles = g.Q * nouter * (g.nx / tx);
+  k<<<tiles, threads, smem, s>>>(g, t, static_cast<typename VT<R>::V*>(W), sp, axis, ltx);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_axis(AxisMode mode, int axis, const Geom& g, const Tables<R>& t, void* W,
+                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s) {
+  switch (mode) {
+    case AXIS_FWD: return launch_axis_m<R, AXIS_FWD>(g, t, W, sp, axis, tx, threads, s);
+    case AXIS_INV: return launch_axis_m<R, AXIS_INV>(g, t, W, sp, axis, tx, threads, s);
+    case AXIS_FGI: return launch_axis_m<R, AXIS_FGI>(g, t, W, sp, axis, tx, threads, s);
+    default: return launch_axis_m<R, AXIS_ENERGY>(g, t, W, sp, axis, tx, threads, s);
+  }
+}
+
+template <typename R>
+cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
+                           double fallback_sigma, cudaStream_t s) {
+  const int threads = 256;
+  long long blocks = (g.P + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  const R fb = (R)fallback_sigma;
+  if (g.n == 1) k_project<R, 1><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
+  else if (g.n == 2) k_project<R, 2><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
+  else k_project<R, 3><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
+  return cudaGetLastError();
+}
+
+#define MBO_INSTANTIATE(R)                                                                     \
+  template cudaError_t launch_row<R>(RowMode, const Geom&, const Tables<R>&, const R*, R*,     \
+                                     void*, const StatsPtrs&, double, int, cudaStream_t);      \
+  template cudaError_t launch_axis<R>(AxisMode, int, const Geom&, const Tables<R>&, void*,     \
+                                      const StatsPtrs&, int, int, cudaStream_t);               \
+  template cudaError_t launch_project<R>(const Geom&, const R*, R*, int8_t*, double,          \
+                                         cudaStream_t);
+
+}  // namespace mbo

@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI in ``include/mbo.h``.
+
+Every function keeps the C name and only marshals arguments: tensors become
+device (or, for the run loop, host) pointers, streams become ``cudaStream_t``
+handles, and outputs are unpacked into Python values.  All arithmetic runs in
+the CUDA library; there is no CPU fallback, and importing a function whose
+library is missing raises.
+
+Fields are ``torch.Tensor`` objects of shape ``(n*n, *dims)`` (channel
+``i*n+j`` = matrix entry ``(i, j)``), contiguous, ``float32`` or ``float64``
+matching the handle's dtype, on the handle's CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MBO_F32 = 1
+MBO_F64 = 2
+MBO_STEP_CONTINUE = 1
+
+STATUS = {0: "MBO_OK", 1: "MBO_ERR_INVALID_ARG", 2: "MBO_ERR_UNSUPPORTED_SIZE", 3: "MBO_ERR_OOM",
+          4: "MBO_ERR_CUDA", 5: "MBO_ERR_NUMERIC", 6: "MBO_ERR_DEVICE_TIMEOUT"}
+
+EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project",
+           "mbo_step", "mbo_lyapunov", "mbo_run_until_stationary", "mbo_profile_enable",
+           "mbo_profile_read", "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
+
+PASSES = ("row_fwd", "axis_fwd", "axis_fgi", "axis_inv", "axis_energy", "row_project", "row_inv",
+          "project")
+
+
+class MboError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mbo_config(C.Structure):
+    _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int)]
+
+
+class mbo_stats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_delta", C.c_double), ("det_flips", C.c_int64),
+                ("fallback_points", C.c_int64), ("nonfinite", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing; build it with "
+                          "paper_1711_01365_gb300.build.build() (nvcc, sm_103a)")
+    L = C.CDLL(path)
+    vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+    L.mbo_default_config.argtypes = [C.POINTER(mbo_config)]
+    L.mbo_default_config.restype = None
+    L.mbo_create.argtypes = [C.POINTER(vp), C.c_int, i64p, C.c_int, C.c_double, C.c_int,
+                             C.POINTER(mbo_config)]
+    L.mbo_destroy.argtypes = [vp]
+    L.mbo_diffuse.argtypes = [vp, vp, vp, vp]
+    L.mbo_project.argtypes = [vp, vp, vp, vp, vp]
+    L.mbo_step.argtypes = [vp, vp, C.c_int, C.POINTER(mbo_stats), vp]
+    L.mbo_lyapunov.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
+    L.mbo_run_until_stationary.argtypes = [vp, vp, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), i64p, C.POINTER(mbo_stats), vp]
+    L.mbo_profile_enable.argtypes = [vp, C.c_int]
+    L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
+    L.mbo_workspace_bytes.argtypes = [vp]
+    L.mbo_workspace_bytes.restype = C.c_int64
+    L.mbo_status_string.argtypes = [C.c_int]
+    L.mbo_status_string.restype = C.c_char_p
+    L.mbo_last_error.argtypes = [vp]
+    L.mbo_last_error.restype = C.c_char_p
+    for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
+              "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, h=None) -> None:
+    if rc != 0:
+        msg = lib().mbo_status_string(rc).decode()
+        if h is not None:
+            detail = lib().mbo_last_error(h).decode()
+            if detail:
+                msg += f" ({detail})"
+        raise MboError(rc, msg)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def mbo_default_config() -> mbo_config:
+    cfg = mbo_config()
+    lib().mbo_default_config(C.byref(cfg))
+    return cfg
+
+
+def mbo_create(dims, n: int, tau: float, dtype: int = MBO_F32, cfg: mbo_config | None = None):
+    """Create a handle for a field of the given dims ((Ny, Nx) or (Nz, Ny, Nx))."""
+    h = C.c_void_p()
+    d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
+    rc = lib().mbo_create(C.byref(h), len(dims), d, int(n), float(tau), int(dtype),
+                          C.byref(cfg) if cfg is not None else None)
+    _check(rc)
+    return h
+
+
+def mbo_destroy(h) -> None:
+    _check(lib().mbo_destroy(h))
+
+
+def mbo_diffuse(h, A, A_tilde, stream=None) -> None:
+    _check(lib().mbo_diffuse(h, _ptr(A), _ptr(A_tilde), _stream(stream)), h)
+
+
+def mbo_project(h, A_tilde, B, det_sign=None, stream=None) -> None:
+    _check(lib().mbo_project(h, _ptr(A_tilde), _ptr(B), _ptr(det_sign), _stream(stream)), h)
+
+
+def mbo_step(h, A, flags: int = 0, want_stats: bool = False, stream=None):
+    st = mbo_stats()
+    _check(lib().mbo_step(h, _ptr(A), int(flags), C.byref(st) if want_stats else None,
+                          _stream(stream)), h)
+    return st.as_dict() if want_stats else None
+
+
+def mbo_lyapunov(h, A, stream=None) -> float:
+    e = C.c_double(0.0)
+    _check(lib().mbo_lyapunov(h, _ptr(A), C.byref(e), _stream(stream)), h)
+    return e.value
+
+
+def mbo_run_until_stationary(h, A, max_steps: int, tol: float, stream=None) -> dict:
+    """Iterate in place; A may be a device tensor or a host array/tensor."""
+    steps = C.c_int(0)
+    stat = C.c_int(0)
+    en = np.zeros(max_steps + 1, dtype=np.float64)
+    md = np.zeros(max(max_steps, 1), dtype=np.float64)
+    fl = np.zeros(max(max_steps, 1), dtype=np.int64)
+    last = mbo_stats()
+    rc = lib().mbo_run_until_stationary(
+        h, _ptr(A), int(max_steps), float(tol), C.byref(steps), C.byref(stat),
+        en.ctypes.data_as(C.POINTER(C.c_double)), md.ctypes.data_as(C.POINTER(C.c_double)),
+        fl.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(last), _stream(stream))
+    _check(rc, h)
+    s = steps.value
+    return {"steps": s, "stationary": bool(stat.value), "energies": en[: s + 1],
+            "max_deltas": md[:s], "det_flips": fl[:s], "last": last.as_dict()}
+
+
+def mbo_profile_enable(h, enable: bool = True) -> None:
+    _check(lib().mbo_profile_enable(h, 1 if enable else 0), h)
+
+
+def mbo_profile_read(h) -> dict:
+    """{pass name: (total ms, launches)} since the last mbo_profile_enable."""
+    n = len(PASSES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(lib().mbo_profile_read(h, ms, cnt, n), h)
+    return {PASSES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def mbo_workspace_bytes(h) -> int:
+    return int(lib().mbo_workspace_bytes(h))
+
+
+def mbo_status_string(status: int) -> str:
+    return lib().mbo_status_string(int(status)).decode()
+
+
+def mbo_last_error(h) -> str:
+    return lib().mbo_last_error(h).decode()
+
+
+class Mbo:
+    """Owning wrapper of a handle (closes it on ``close()`` / garbage collection)."""
+
+    def __init__(self, dims, n: int, tau: float, dtype: str = "f32", **cfg):
+        c = mbo_default_config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.dims, self.n, self.tau = tuple(int(d) for d in dims), int(n), float(tau)
+        self.dtype = {"f32": MBO_F32, "f64": MBO_F64}[dtype]
+        self.h = mbo_create(self.dims, self.n, self.tau, self.dtype, c)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            mbo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def diffuse(self, A, out, stream=None):
+        mbo_diffuse(self.h, A, out, stream)
+        return out
+
+    def project(self, At, out, det_sign=None, stream=None):
+        mbo_project(self.h, At, out, det_sign, stream)
+        return out
+
+    def step(self, A, flags=0, want_stats=False, stream=None):
+        return mbo_step(self.h, A, flags, want_stats, stream)
+
+    def lyapunov(self, A, stream=None) -> float:
+        return mbo_lyapunov(self.h, A, stream)
+
+    def run(self, A, max_steps: int, tol: float, stream=None) -> dict:
+        return mbo_run_until_stationary(self.h, A, max_steps, tol, stream)
