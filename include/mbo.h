@@ -6,10 +6,10 @@
  * (arXiv:1711.01365) on a flat torus [0,1)^d, d = 2 or 3:
  *   diffusion  (Sec. 5.1): every entry A_ij is advanced by the periodic heat
  *              semigroup, A~ = iFFT( g(k) FFT(A_ij) ), g(k) = exp(-4 pi^2 tau |k|^2);
- *   projection (Lemma 2.1): every grid point becomes U V^t, the closest
+ *   projection (Lemma 1.1): every grid point becomes U V^t, the closest
  *              orthogonal matrix to A~(x) = U S V^t, whose determinant has the
  *              sign of det A~(x) (det A~ = 0 -> +1; A~ = 0 -> identity);
- *   Lyapunov functional (Eq. 4.1): E(A) = (prod h_j / tau) sum_x (n - <A, e^{tau Lap} A>_F);
+ *   Lyapunov functional (Sec. 4): E(A) = (prod h_j / tau) sum_x (n - <A, e^{tau Lap} A>_F);
  *   stationarity (Prop. 4.6): a step is stationary when no point changes its
  *              determinant sign and every entry moves by at most tol.
  *
@@ -73,7 +73,7 @@ typedef struct {
 
 /* Per-step record.  Step s maps A_{s} to A_{s+1}. */
 typedef struct {
-  double energy;           /* E^tau(A_s), accumulated in FP64 (Eq. 4.1)          */
+  double energy;           /* E^tau(A_s), accumulated in FP64 (Sec. 4)            */
   double max_delta;        /* max over points and channels |A_{s+1} - A_s|        */
   int64_t det_flips;       /* points where sign det A_{s+1} != sign det A_s       */
   int64_t fallback_points; /* MBO_F32: points re-projected in FP64                */
@@ -99,7 +99,7 @@ MBO_API mbo_status mbo_destroy(mbo_handle h);
  * A and A_tilde are device fields (they may be the same pointer). */
 MBO_API mbo_status mbo_diffuse(mbo_handle h, const void* A, void* A_tilde, void* stream);
 
-/* Projection step of Algorithm 1 alone (Lemma 2.1): B(x) = polar factor of
+/* Projection step of Algorithm 1 alone (Lemma 1.1): B(x) = polar factor of
  * A_tilde(x).  det_sign (nullable, int8 per point) receives +1 or -1, the
  * class chosen for B.  A_tilde and B may be the same pointer. */
 MBO_API mbo_status mbo_project(mbo_handle h, const void* A_tilde, void* B, int8_t* det_sign,
@@ -116,7 +116,7 @@ MBO_API mbo_status mbo_project(mbo_handle h, const void* A_tilde, void* B, int8_
  * record of this step (energy is that of the input field). */
 MBO_API mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* stream);
 
-/* Lyapunov functional E^tau(A) (Eq. 4.1), in its Parseval form
+/* Lyapunov functional E^tau(A) (Sec. 4), in its Parseval form
  *   (1/(P tau)) [ (1/P) sum_k (1 - g(k)) sum_c |A^_c(k)|^2 + sum_x (n - |A(x)|_F^2) ],
  * accumulated in FP64.  Synchronises the stream; result in *E. */
 MBO_API mbo_status mbo_lyapunov(mbo_handle h, const void* A, double* E, void* stream);

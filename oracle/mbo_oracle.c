@@ -13,10 +13,10 @@
  *      with the periodic heat kernel G_{p,tau}; on the grid this is
  *      iFFT( g(k) * FFT(A_ij) ) with the exact torus multiplier
  *      g(k) = exp(-4 pi^2 tau |k|^2), k the signed integer frequency.
- *   2. Projection step (Lemma 2.1, "l:proj"): at every grid point the diffused
+ *   2. Projection step (Lemma 1.1): at every grid point the diffused
  *      matrix is replaced by U V^t from its SVD, the closest orthogonal matrix,
  *      whose determinant sign equals that of the diffused matrix.
- *   3. Lyapunov functional (Eq. 4.1, "eq:Lyapunov"), discretised with the
+ *   3. Lyapunov functional (Sec. 4, the functional E^tau), discretised with the
  *      quadrature weight prod_j h_j:
  *        E^tau(A) = (prod h_j / tau) * sum_x ( n - <A(x), (e^{tau Delta} A)(x)>_F ).
  *   4. Stationarity: a step is stationary when no grid point changes the sign
@@ -32,7 +32,7 @@
  *   - the multiplier is the exact exp(-4 pi^2 tau |k|^2), not the DFT of the
  *     sampled periodic kernel (they differ by aliasing terms ~exp(-pi^2 N^2 tau));
  *   - at det(A~) = 0 the positive class is chosen; A~ = 0 maps to the identity;
- *   - the energy constant is n (Eq. 4.1), with quadrature weight prod h_j.
+ *   - the energy constant is n (Sec. 4), with quadrature weight prod h_j.
  */
 #include <complex.h>
 #include <math.h>
@@ -231,7 +231,7 @@ int orc_diffuse(const double* A, double* At, int ndim, const int64_t* dims, int 
 }
 
 /* ------------------------------------------------------------------------- */
-/* Projection (Lemma 2.1): one-sided Jacobi SVD and the polar factor U V^t     */
+/* Projection (Lemma 1.1): one-sided Jacobi SVD and the polar factor U V^t     */
 /* ------------------------------------------------------------------------- */
 
 /* Determinant by Gaussian elimination with partial pivoting (row-major n x n). */
@@ -283,7 +283,7 @@ static void complete_column(double* U, int n, int col, const int* have) {
 
 /* Polar factor of one n x n matrix M (row-major) by a one-sided (Hestenes)
  * Jacobi SVD.  B = U D V^t where D = I except that the entry of the smallest
- * singular value is chosen so that sign det B = sign det M (Lemma 2.1; at
+ * singular value is chosen so that sign det B = sign det M (Lemma 1.1; at
  * det M = 0 the positive class).  For nonsingular M this is exactly U V^t of
  * the SVD; the flip form is the opposite-class minimiser of Lemma 7.1.
  * sigma (nullable) receives the singular values in descending order.
@@ -385,7 +385,7 @@ int orc_project_field(const double* At, double* B, int8_t* det_sign, int64_t P, 
 }
 
 /* ------------------------------------------------------------------------- */
-/* Lyapunov functional (Eq. 4.1 and its grid sum in Sec. 4.1)                 */
+/* Lyapunov functional (Sec. 4 and its grid sum in Sec. 4.1)                 */
 /* ------------------------------------------------------------------------- */
 
 static double quad_weight(int ndim, const int64_t* dims) {

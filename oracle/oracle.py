@@ -4,7 +4,7 @@ Test infrastructure only: the tests, the smoke check and the benchmark's
 CPU-baseline leg load it; the CUDA library never does.  Every function here
 marshals numpy arrays into the C routines, which follow Algorithm 1 of
 Osting & Wang (arXiv:1711.01365): the diffusion step of Sec. 5.1, the
-projection of Lemma 2.1, and the Lyapunov functional of Eq. 4.1.
+projection of Lemma 1.1, and the Lyapunov functional of Sec. 4.
 
 Field layout: float64 array of shape ``(n*n, *dims)``, channel ``i*n+j`` holding
 matrix entry ``(i, j)`` at every grid point.
@@ -142,7 +142,7 @@ def det(M: np.ndarray) -> float:
 
 
 def polar(M: np.ndarray, return_sigma: bool = False):
-    """Closest orthogonal matrix of one n x n matrix (Lemma 2.1)."""
+    """Closest orthogonal matrix of one n x n matrix (Lemma 1.1)."""
     M = _f64(M)
     n = M.shape[0]
     B = np.empty_like(M)
@@ -170,7 +170,7 @@ def energy_from(A: np.ndarray, At: np.ndarray, n: int, tau: float) -> float:
 
 
 def energy(A: np.ndarray, n: int, tau: float) -> float:
-    """E^tau(A), physical form (Eq. 4.1 with weight prod h_j)."""
+    """E^tau(A), physical form (Sec. 4 functional with weight prod h_j)."""
     A = _f64(A)
     return _load().orc_energy(_dp(A), A.ndim - 1, _dims(A.shape[1:]), n, float(tau))
 

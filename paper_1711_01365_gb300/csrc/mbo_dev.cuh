@@ -1,6 +1,6 @@
 // Device building blocks of the GB300 MBO path: complex arithmetic, small
 // register DFTs, in-place mixed-radix transforms over sequences held in shared
-// memory, the per-point closest-orthogonal-matrix projections (Lemma 2.1 of
+// memory, the per-point closest-orthogonal-matrix projections (Lemma 1.1 of
 // Osting & Wang, arXiv:1711.01365) and block reductions.
 #pragma once
 #include <cuda_runtime.h>
@@ -233,7 +233,7 @@ __device__ void fft_inv(V* s, const L& lay, int N, int M, const Plan& pl, const 
 }
 
 // ---------------------------------------------------------------------------
-// Closest orthogonal matrix (Lemma 2.1).  Input m and output b are row-major
+// Closest orthogonal matrix (Lemma 1.1).  Input m and output b are row-major
 // n x n.  Returns the class sign s = +1 if det m >= 0 else -1 (det b = s) and
 // the smallest singular value of m in smin.
 // ---------------------------------------------------------------------------
@@ -407,7 +407,7 @@ template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& s
 //   X <- (zeta X + X^{-t} / zeta) / 2,  zeta = (|X^{-1}|_F / |X|_F)^{1/2},
 // with X^{-t} = cof(X) / det(X).  Each iterate keeps the singular vectors of
 // m (the singular values s map to (zeta s + 1/(zeta s)) / 2), so the limit is
-// U V^t of Lemma 2.1 and det X keeps the sign of det m.  Stops when an update
+// U V^t of Lemma 1.1 and det X keeps the sign of det m.  Stops when an update
 // moves X by less than sqrt(tol2) (quadratic convergence) or after ITMAX
 // iterations.  est receives |det m| / |cof m|_F, which lies in
 // [sigma_min / sqrt(3), sigma_min]; callers route points with small est (and

@@ -14,9 +14,9 @@
 // (spectrum left digit-reversed along that axis), inverse DIT.
 // Passes of one step (steady state, 2-D):
 //   k_axis<FGI>   along y: forward DFT, x g(k)/P (Sec. 5.1), energy partials
-//                 (Eq. 4.1, Parseval form), inverse DFT
+//                 (Sec. 4 functional, Parseval form), inverse DFT
 //   k_row<INV_PROJECT_FWD> along x: inverse DFT, per-point polar factor
-//                 (Lemma 2.1), step statistics, then the forward x-DFT of the
+//                 (Lemma 1.1), step statistics, then the forward x-DFT of the
 //                 new field for the next step
 // 3-D adds k_axis<FWD> and k_axis<INV> along y around the z pass.
 #pragma once

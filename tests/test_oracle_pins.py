@@ -149,7 +149,7 @@ def test_maximum_principle(n):
 
 
 # --------------------------------------------------------------------------
-# Projection (Lemma 2.1; P5)
+# Projection (Lemma 1.1; P5)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
@@ -346,7 +346,7 @@ def test_n1_is_classical_mbo_and_terminates_exactly():
 
 
 def test_so2_data_reduces_to_complex_mbo():
-    """Lemma 3.1 / Sec. 2: SO(2) data stay SO(2) and the step is z <- Gz/|Gz|
+    """Lemma 1.3 / Sec. 1: SO(2) data stay SO(2) and the step is z <- Gz/|Gz|
     for z = a + i b (computed here independently with numpy.fft)."""
     dims = (32, 32)
     tau = 4.0 / 32 ** 2
