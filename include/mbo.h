@@ -158,6 +158,41 @@ enum {
 MBO_API mbo_status mbo_profile_enable(mbo_handle h, int enable);
 MBO_API mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npass);
 
+/* Diffusion without any device allocation.
+ *
+ * Same result as mbo_diffuse (A_tilde = e^{tau Lap} A on the grid given by
+ * ndim/dims, n, tau and dtype, as in mbo_create), but without a handle and
+ * without calling cudaMalloc, cudaFree or any allocating routine.  It is meant
+ * for callers that must not allocate device memory: code that runs while a
+ * framework's caching allocator already holds the device memory it is allowed
+ * to use, loops that cannot take the synchronisation that cudaMalloc/cudaFree
+ * may imply, and programs whose device memory budget is fixed in advance.  The
+ * paper has no counterpart of this entry point; it only changes where the
+ * scratch memory lives.
+ *
+ * Scratch: one statically sized device array of MBO_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) inside this library.  Every GPU that loads the library keeps it
+ * until the process exits.  A call needs ceil(n*n/2) * prod(dims) * 2 * w
+ * bytes of workspace (w = 4 for MBO_F32, 8 for MBO_F64) plus under 100 KB of
+ * tables; a larger problem (for example 1024 x 1024 with n = 3 in MBO_F64)
+ * returns MBO_ERR_UNSUPPORTED_SIZE and does nothing.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents.
+ *     Every call writes the tables and workspace it reads before reading them,
+ *     so nothing needs clearing; but calls that overlap on the GPU (different
+ *     streams, or host threads without ordering) race on the array: order them,
+ *     for example by using one stream.
+ * A and A_tilde: caller-owned, 16-byte-aligned device fields (may be equal).
+ * Asynchronous on stream.  Errors: MBO_ERR_INVALID_ARG (bad argument or
+ * pointer), MBO_ERR_UNSUPPORTED_SIZE (axis length, or scratch too small),
+ * MBO_ERR_CUDA (a launch or the address lookup failed). */
+#define MBO_NOALLOC_SCRATCH_BYTES (64u << 20)
+MBO_API mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, double tau,
+                                       mbo_dtype dtype, const void* A, void* A_tilde,
+                                       void* stream);
+
 /* Bytes of device memory the handle holds (workspace and tables). */
 MBO_API int64_t mbo_workspace_bytes(mbo_handle h);
 

@@ -25,82 +25,6 @@ size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback) {
 }
 size_t axis_smem_bytes(int len, int tx, size_t elem_bytes) { return (size_t)len * tx * 2 * elem_bytes; }
 
-}  // namespace mbo
-
-using namespace mbo;
-
-struct mbo_ctx {
-  int dev = 0;
-  Geom g{};
-  int64_t dims_user[3] = {0, 0, 0};
-  mbo_dtype dtype = MBO_F32;
-  mbo_config cfg{};
-  size_t elem = 4;
-  // device memory
-  void* W = nullptr;
-  void* tabs = nullptr;  // twiddles, multipliers (one allocation)
-  size_t tabs_bytes = 0;
-  double* part = nullptr;
-  RunState* st = nullptr;
-  Hist hist{};
-  void* hist_mem = nullptr;
-  void* field = nullptr;  // staging field for host-pointer runs
-  // host mirrors
-  RunState* h_st = nullptr;  // pinned
-  void* h_hist = nullptr;    // pinned ring copy
-  // launch configuration
-  Tables<float> tf{};
-  Tables<double> td{};
-  int row_threads = 256, axis_threads = 256, tx = 8;
-  size_t bytes_total = 0;
-  // workspace validity for MBO_STEP_CONTINUE
-  const void* w_valid_for = nullptr;
-  // captured step graph
-  cudaStream_t cap = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const void* g_ptr = nullptr;
-  double g_tol = 0;
-  // per-pass device timing (mbo_profile_*)
-  bool prof = false;
-  std::vector<cudaEvent_t> ev_free;
-  struct Pending { int pass; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
-  double prof_ms[MBO_PROFILE_PASSES] = {0};
-  long long prof_n[MBO_PROFILE_PASSES] = {0};
-  char err[512] = {0};
-};
-
-namespace {
-
-mbo_status fail(mbo_ctx* h, mbo_status s, const char* fmt, ...) {
-  if (h) {
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(h->err, sizeof(h->err), fmt, ap);
-    va_end(ap);
-  }
-  return s;
-}
-
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return fail(h, e_ == cudaErrorMemoryAllocation ? MBO_ERR_OOM : MBO_ERR_CUDA,        \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
-  } while (0)
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
 bool factor23(int64_t N, int& a, int& b) {
   a = b = 0;
   while (N % 2 == 0) { N /= 2; ++a; }
@@ -180,6 +104,82 @@ int pick_tx(int nx, int cap) {
   while (t < cap && nx % (2 * t) == 0) t *= 2;
   return t;
 }
+
+}  // namespace mbo
+
+using namespace mbo;
+
+struct mbo_ctx {
+  int dev = 0;
+  Geom g{};
+  int64_t dims_user[3] = {0, 0, 0};
+  mbo_dtype dtype = MBO_F32;
+  mbo_config cfg{};
+  size_t elem = 4;
+  // device memory
+  void* W = nullptr;
+  void* tabs = nullptr;  // twiddles, multipliers (one allocation)
+  size_t tabs_bytes = 0;
+  double* part = nullptr;
+  RunState* st = nullptr;
+  Hist hist{};
+  void* hist_mem = nullptr;
+  void* field = nullptr;  // staging field for host-pointer runs
+  // host mirrors
+  RunState* h_st = nullptr;  // pinned
+  void* h_hist = nullptr;    // pinned ring copy
+  // launch configuration
+  Tables<float> tf{};
+  Tables<double> td{};
+  int row_threads = 256, axis_threads = 256, tx = 8;
+  size_t bytes_total = 0;
+  // workspace validity for MBO_STEP_CONTINUE
+  const void* w_valid_for = nullptr;
+  // captured step graph
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_ptr = nullptr;
+  double g_tol = 0;
+  // per-pass device timing (mbo_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pending { int pass; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double prof_ms[MBO_PROFILE_PASSES] = {0};
+  long long prof_n[MBO_PROFILE_PASSES] = {0};
+  char err[512] = {0};
+};
+
+namespace {
+
+mbo_status fail(mbo_ctx* h, mbo_status s, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? MBO_ERR_OOM : MBO_ERR_CUDA,        \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 template <typename R> struct TabBuild {
   std::vector<unsigned char> bytes;

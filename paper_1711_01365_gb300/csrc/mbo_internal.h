@@ -105,6 +105,13 @@ template <typename R>
 cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
                            double fallback_sigma, cudaStream_t s);
 
+// Plan helpers (mbo_api.cu).
+bool factor23(int64_t N, int& a, int& b);
+FastDiv make_div(unsigned d);
+Plan make_plan(int N);
+int plan_twiddles(const Plan& p);
+int pick_tx(int nx, int cap);
+
 // Shared memory bytes of the row kernel for a geometry.
 size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback);
 size_t axis_smem_bytes(int len, int tx, size_t elem_bytes);

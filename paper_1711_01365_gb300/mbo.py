@@ -28,7 +28,10 @@ STATUS = {0: "MBO_OK", 1: "MBO_ERR_INVALID_ARG", 2: "MBO_ERR_UNSUPPORTED_SIZE", 
 
 EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project",
            "mbo_step", "mbo_lyapunov", "mbo_run_until_stationary", "mbo_profile_enable",
-           "mbo_profile_read", "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
+           "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_workspace_bytes", "mbo_status_string",
+           "mbo_last_error")
+
+MBO_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 PASSES = ("row_fwd", "axis_fwd", "axis_fgi", "axis_inv", "axis_energy", "row_project", "row_inv",
           "project")
@@ -84,6 +87,7 @@ def lib():
                                            C.POINTER(C.c_double), i64p, C.POINTER(mbo_stats), vp]
     L.mbo_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
+    L.mbo_diffuse_noalloc.argtypes = [C.c_int, i64p, C.c_int, C.c_double, C.c_int, vp, vp, vp]
     L.mbo_workspace_bytes.argtypes = [vp]
     L.mbo_workspace_bytes.restype = C.c_int64
     L.mbo_status_string.argtypes = [C.c_int]
@@ -91,7 +95,8 @@ def lib():
     L.mbo_last_error.argtypes = [vp]
     L.mbo_last_error.restype = C.c_char_p
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
-              "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read"):
+              "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
+              "mbo_diffuse_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -183,6 +188,14 @@ def mbo_run_until_stationary(h, A, max_steps: int, tol: float, stream=None) -> d
     s = steps.value
     return {"steps": s, "stationary": bool(stat.value), "energies": en[: s + 1],
             "max_deltas": md[:s], "det_flips": fl[:s], "last": last.as_dict()}
+
+
+def mbo_diffuse_noalloc(dims, n: int, tau: float, dtype: int, A, A_tilde, stream=None) -> None:
+    """mbo_diffuse without a handle and without device allocation (scratch in a
+    static 64 MiB device array inside the library; see include/mbo.h)."""
+    d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
+    _check(lib().mbo_diffuse_noalloc(len(dims), d, int(n), float(tau), int(dtype), _ptr(A),
+                                     _ptr(A_tilde), _stream(stream)))
 
 
 def mbo_profile_enable(h, enable: bool = True) -> None:
