@@ -69,6 +69,12 @@ typedef struct {
                             many steps to test for stationarity (default 16).    */
   int use_graph;         /* run loop: replay the step from a captured CUDA graph
                             (default 1).                                          */
+  int row_threads;       /* launch shape of the x-axis (row) pass: threads per
+                            block, a multiple of 32 in [32, 384]; 0 = automatic.  */
+  int axis_threads;      /* threads per block of the y / z passes, a multiple of
+                            32 in [64, 384]; 0 = automatic.                       */
+  int axis_tx;           /* x-columns per block of the y / z passes: a power of
+                            two dividing Nx, at most 16; 0 = automatic.           */
 } mbo_config;
 
 /* Per-step record.  Step s maps A_{s} to A_{s+1}. */

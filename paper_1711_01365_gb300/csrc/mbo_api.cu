@@ -215,7 +215,7 @@ void build_tables(mbo_ctx* h, TabBuild<R>& tb, Tables<R>& t) {
         for (int j = 1; j < s.rad; ++j) {
           const long long e = ((long long)n1 * j) % s.lb;
           const double ang = 2.0 * pi * (double)e / (double)s.lb;
-          const size_t i = (size_t)s.tw + (size_t)n1 * (s.rad - 1) + (j - 1);
+          const size_t i = (size_t)s.tw + (size_t)(j - 1) * s.m + n1;
           tw[2 * i] = (R)std::cos(ang);
           tw[2 * i + 1] = (R)(-std::sin(ang));
         }
@@ -371,6 +371,9 @@ void mbo_default_config(mbo_config* cfg) {
   cfg->fallback_sigma = 1e-3;
   cfg->check_interval = 16;
   cfg->use_graph = 1;
+  cfg->row_threads = 0;
+  cfg->axis_threads = 0;
+  cfg->axis_tx = 0;
 }
 
 int64_t mbo_workspace_bytes(mbo_handle h) { return h ? (int64_t)h->bytes_total : 0; }
@@ -430,8 +433,33 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   cudaGetDevice(&h->dev);
   // launch shapes
   h->tx = pick_tx(g.nx, dtype == MBO_F32 ? 8 : 4);
-  h->row_threads = g.nx >= 1024 ? 256 : (g.nx >= 256 ? 128 : (g.nx >= 64 ? 64 : 32));
+  // measured on GB300 (1024^2, n = 3): 192 threads best for FP32 rows, 128 for FP64
+  h->row_threads = g.nx >= 2048 ? 256
+                   : g.nx >= 1024 ? (dtype == MBO_F32 ? 192 : 128)
+                   : (g.nx >= 256 ? 128 : (g.nx >= 64 ? 64 : 32));
   h->axis_threads = 256;
+  const mbo_config& c = h->cfg;
+  if (c.row_threads) {
+    if (c.row_threads < 32 || c.row_threads > kMaxThreads || c.row_threads % 32) {
+      delete h;
+      return MBO_ERR_INVALID_ARG;
+    }
+    h->row_threads = c.row_threads;
+  }
+  if (c.axis_tx) {
+    if (c.axis_tx < 1 || c.axis_tx > 16 || (c.axis_tx & (c.axis_tx - 1)) || g.nx % c.axis_tx) {
+      delete h;
+      return MBO_ERR_INVALID_ARG;
+    }
+    h->tx = c.axis_tx;
+  }
+  if (c.axis_threads) {
+    if (c.axis_threads < 64 || c.axis_threads > kMaxThreads || c.axis_threads % 32) {
+      delete h;
+      return MBO_ERR_INVALID_ARG;
+    }
+    h->axis_threads = c.axis_threads;
+  }
   const size_t rs = row_smem_bytes(g, h->elem, true);
   const size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
   int maxsm = 0;

@@ -137,7 +137,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 //   RowLayout: sequence m at m*S, element p at p + p/16 (one pad slot per 16
 //              elements keeps short-span butterflies free of bank conflicts);
 //              butterflies map sequence-major (consecutive threads, consecutive j).
-//   ColLayout: element (m, p) at p*M + m (a tile of M = 2^ltx adjacent columns);
+//   ColLayout: element (m, p) at row p (swizzled, see addr) column m of a tile
+//              of M = 2^ltx adjacent columns;
 //              butterflies map column-fastest.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int row_pad(int N) { return N + (N >> 4) + 1; }
@@ -150,7 +151,13 @@ struct RowLayout {
 struct ColLayout {
   static constexpr bool kColumns = true;
   int ltx;
-  __device__ __forceinline__ int addr(int m, int p) const { return (p << ltx) + m; }
+  int swz;  // 1 when the axis length is even (the swizzle pairs rows 2k, 2k+1), else 0
+  // Row p of the tile is stored at row p ^ b, b = bit 0 of (p >> 3) ^ (p >> 4):
+  // butterflies of the short-span stages, whose rows are 8 or 16 apart, then
+  // alternate between the two 64-byte halves of a 128-byte bank line.
+  __device__ __forceinline__ int addr(int m, int p) const {
+    return ((p ^ (((p >> 3) ^ (p >> 4)) & swz)) << ltx) + m;
+  }
 };
 
 // In-place mixed-radix transforms.  The forward transform is a decimation-in-
@@ -186,16 +193,16 @@ __device__ __forceinline__ void radix_stage(V* s, const L& lay, int N, int M, co
     if (DIR < 0) {
       dft<-1, RAD>(v);
       if (m > 1) {
-        const V* t = tws + n1 * (RAD - 1);
+        const V* t = tws + n1;
 #pragma unroll
-        for (int j = 1; j < RAD; ++j) v[j] = cmul(v[j], __ldg(&t[j - 1]));
+        for (int j = 1; j < RAD; ++j) v[j] = cmul(v[j], __ldg(&t[(j - 1) * m]));
       }
     } else {
       if (m > 1) {
-        const V* t = tws + n1 * (RAD - 1);
+        const V* t = tws + n1;
 #pragma unroll
         for (int j = 1; j < RAD; ++j) {
-          V c = __ldg(&t[j - 1]);
+          V c = __ldg(&t[(j - 1) * m]);
           c.y = -c.y;
           v[j] = cmul(v[j], c);
         }
@@ -403,56 +410,86 @@ template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& s
   return sg;
 }
 
+// Reciprocal of a nonzero value: correctly rounded in FP32; in FP64 an FP32
+// seed refined by two Newton steps (relative error at FP64 rounding level).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+}
+
+// Cofactor matrix of a row-major 3x3 X (so X^{-t} = cof(X) / det X) and det X.
+template <typename R> __device__ __forceinline__ R cofactor3(const R* X, R* C) {
+  C[0] = X[4] * X[8] - X[5] * X[7];
+  C[1] = X[5] * X[6] - X[3] * X[8];
+  C[2] = X[3] * X[7] - X[4] * X[6];
+  C[3] = X[2] * X[7] - X[1] * X[8];
+  C[4] = X[0] * X[8] - X[2] * X[6];
+  C[5] = X[1] * X[6] - X[0] * X[7];
+  C[6] = X[1] * X[5] - X[2] * X[4];
+  C[7] = X[2] * X[3] - X[0] * X[5];
+  C[8] = X[0] * X[4] - X[1] * X[3];
+  return X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+}
+
 // n = 3, scaled Newton iteration for the polar factor (Higham 1986):
 //   X <- (zeta X + X^{-t} / zeta) / 2,  zeta = (|X^{-1}|_F / |X|_F)^{1/2},
-// with X^{-t} = cof(X) / det(X).  Each iterate keeps the singular vectors of
-// m (the singular values s map to (zeta s + 1/(zeta s)) / 2), so the limit is
-// U V^t of Lemma 1.1 and det X keeps the sign of det m.  Stops when an update
-// moves X by less than sqrt(tol2) (quadratic convergence) or after ITMAX
-// iterations.  est receives |det m| / |cof m|_F, which lies in
+// with X^{-t} = cof(X) / det(X).  With X = Q H, cof(X) = det(X) Q H^{-1}, so
+// a X + c cof(X) = Q (a H + c det(X) H^{-1}) keeps the polar factor Q for any
+// a > 0 and c det(X) > 0: the scaled phase only sets the speed, and its
+// coefficients are computed in FP32 whatever R is.  The scaled phase ends
+// when |X|_F^2 = sum s_i^2 is within 1e-4 of 3 and zeta within 1e-5 of 1:
+// then sum s_i^2 * sum s_i^-2 is within ~1e-4 of 9, its minimum, which by the
+// AM-HM inequality holds only when every s_i^2 is close to 1 (zeta = 1 alone
+// does not suffice: s = (2, 1/2, 1) gives zeta = 1).  NUN unscaled iterations
+// X <- (X + X^{-t}) / 2 follow; each squares the distance to orthogonality
+// (d -> d^2 / 2) and their fixed point is exactly orthogonal.  det X keeps
+// the sign of det m.  est receives |det m| / |cof m|_F, which lies in
 // [sigma_min / sqrt(3), sigma_min]; callers route points with small est (and
 // exactly singular ones, where the iteration is undefined) elsewhere.
-template <int ITMAX, typename R>
-__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R tol2) {
-  R X[9];
+template <int ITMAX, int NUN, typename R>
+__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est) {
+  R X[9], C[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) X[k] = m[k];
-  R sg = R(1);
+  R det = cofactor3(X, C);
+  const R sg = (det >= R(0)) ? R(1) : R(-1);
+  {
+    R nc = R(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
+    est = fabs(det) * rsqrt_(nc);
+  }
+  if (!(est > R(0))) {  // singular or not finite: caller's fallback
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b[k] = X[k];
+    return sg;
+  }
 #pragma unroll 1
   for (int it = 0; it < ITMAX; ++it) {
-    R C[9];
-    C[0] = X[4] * X[8] - X[5] * X[7];
-    C[1] = X[5] * X[6] - X[3] * X[8];
-    C[2] = X[3] * X[7] - X[4] * X[6];
-    C[3] = X[2] * X[7] - X[1] * X[8];
-    C[4] = X[0] * X[8] - X[2] * X[6];
-    C[5] = X[1] * X[6] - X[0] * X[7];
-    C[6] = X[1] * X[5] - X[2] * X[4];
-    C[7] = X[2] * X[3] - X[0] * X[5];
-    C[8] = X[0] * X[4] - X[1] * X[3];
-    const R det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
-    R nx = R(0), nc = R(0);
+    float nx = 0.f, nc = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      nx += X[k] * X[k];
-      nc += C[k] * C[k];
+      nx += (float)X[k] * (float)X[k];
+      nc += (float)C[k] * (float)C[k];
     }
-    if (it == 0) {
-      sg = (det >= R(0)) ? R(1) : R(-1);
-      est = fabs(det) * rsqrt_(nc);
-      if (!(est > R(0))) break;  // singular or not finite: caller's fallback
-    }
-    const R zeta = sqrt(sqrt(nc / (det * det * nx)));
-    const R a = R(0.5) * zeta;
-    const R c = R(0.5) / (zeta * det);
-    R diff = R(0);
+    const float fd = (float)det;
+    const float zf = rsqrtf(rsqrtf(__fdividef(nc, fd * fd * nx)));  // (nc / (det^2 nx))^{1/4}
+    if (fabsf(zf - 1.0f) < 1e-5f && fabsf(nx - 3.0f) < 1e-4f) break;
+    const R a = R(0.5f * zf);
+    const R c = R(__fdividef(0.5f, zf * fd));
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const R xn = a * X[k] + c * C[k];
-      diff += (xn - X[k]) * (xn - X[k]);
-      X[k] = xn;
-    }
-    if (diff < tol2) break;
+    for (int k = 0; k < 9; ++k) X[k] = a * X[k] + c * C[k];
+    det = cofactor3(X, C);
+  }
+#pragma unroll
+  for (int it = 0; it < NUN; ++it) {
+    const R c = R(0.5) * recip(det);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = R(0.5) * X[k] + c * C[k];
+    if (it + 1 < NUN) det = cofactor3(X, C);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) b[k] = X[k];
@@ -474,7 +511,7 @@ template <int NM> __device__ __forceinline__ double polar_f64(const double* m, d
 #pragma unroll
     for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
     double est = 0.0;
-    const double sg = polar3_newton<16>(m, b, est, 1e-22);
+    const double sg = polar3_newton<16, 3>(m, b, est);
     smin = est;
     if (est > 1e-12 * sqrt(nx)) return sg;
     return polar3(m, b, smin);

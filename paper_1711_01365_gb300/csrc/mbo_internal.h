@@ -8,7 +8,9 @@ namespace mbo {
 
 constexpr int kMaxStages = 8;
 constexpr int kRing = 1024;      // step-record ring (power of two)
-constexpr int kMaxThreads = 512; // row and axis kernels are launched with <= this many threads
+// Row and axis kernels are launched with at most this many threads and are
+// compiled so that 768 (FP32) or 384 (FP64) threads fit on an SM.
+constexpr int kMaxThreads = 384;
 constexpr int kFallbackCap = 64; // per-row FP64 re-projection slots (FP32 path)
 
 // Division of x < 65536 by a fixed d < 65536: a shift when d is a power of
@@ -22,7 +24,8 @@ struct FastDiv {
 // One forward stage: radix rad on blocks of length lb = N / (rad_0 ... rad_{st-1});
 // a butterfly (block b, offset n1 < m = lb / rad) owns positions b*lb + n1 + m*j.
 // tw is the offset of the stage's twiddles exp(-2 pi i n1 j / lb), stored
-// [n1][j - 1], in the axis twiddle table (unused when m == 1).
+// [j - 1][n1] (n1 fastest, so lanes with consecutive n1 read consecutive
+// entries), in the axis twiddle table (unused when m == 1).
 struct Stage {
   int rad, lb, m, tw;
   FastDiv dm;   // division by m

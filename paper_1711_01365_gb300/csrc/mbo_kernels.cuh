@@ -48,7 +48,7 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
     float est = 0.f;
-    sg = polar3_newton<10>(m, b, est, 1e-10f);
+    sg = polar3_newton<10, 2>(m, b, est);
     return !(est < fb) && est > 1e-6f * sqrtf(nx);
   } else {
     float sm;
@@ -93,7 +93,7 @@ __device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, lon
 }
 
 template <typename R, int NM, int MODE>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, sizeof(R) == 4 ? 2 : 1)
 k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W, StatsPtrs sp,
       R fb_sigma) {
   using V = typename VT<R>::V;
@@ -265,7 +265,7 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
 // Strided-axis pass (y in 2-D; y and z in 3-D).  One block owns a tile of tx
 // adjacent x-columns of one complex plane along the whole axis.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, sizeof(R) == 4 ? 2 : 1)
 k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int ltx) {
   using V = typename VT<R>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -287,7 +287,7 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   const int o = rem / xt;
   const int x0 = (rem - o * xt) << ltx;
   V* base = W + (long long)q * g.P + (long long)o * ostride + x0;
-  const ColLayout lay{ltx};
+  const ColLayout lay{ltx, (L & 1) ? 0 : 1};
   const int T = blockDim.x, tid = threadIdx.x;
   const V* tw = static_cast<const V*>(t.tw[axis]);
 
@@ -298,7 +298,7 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   const long long gstep = (long long)dp * es;
   {
     const V* src = base + mcol + (long long)p0 * es;
-    for (int p = p0; p < L; p += dp, src += gstep) cp_async_elem(&s[(p << ltx) + mcol], src);
+    for (int p = p0; p < L; p += dp, src += gstep) cp_async_elem(&s[lay.addr(mcol, p)], src);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -320,7 +320,7 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
     const R fo = gxx * go * t.inv_p;
     const R omo2 = gxx * go;
     for (int p = p0; p < L; p += dp) {
-      const int e = (p << ltx) + mcol;
+      const int e = lay.addr(mcol, p);
       const R omv = omx + gxx * omo + omo2 * omL[p];  // 1 - g without cancellation
       V z = s[e];
       acc += omv * (z.x * z.x + z.y * z.y);
@@ -334,7 +334,7 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   if (MODE == AXIS_FGI || MODE == AXIS_INV) fft_inv(s, lay, L, tx, t.plan[axis], tw);
   if (MODE != AXIS_ENERGY) {
     V* dst = base + mcol + (long long)p0 * es;
-    for (int p = p0; p < L; p += dp, dst += gstep) *dst = s[(p << ltx) + mcol];
+    for (int p = p0; p < L; p += dp, dst += gstep) *dst = s[lay.addr(mcol, p)];
   }
   if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
     const double tot = block_sum((double)acc, redd);

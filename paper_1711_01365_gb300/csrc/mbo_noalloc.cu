@@ -39,7 +39,7 @@ cudaError_t scratch_address(int dev, void** out) {
   return cudaSuccess;
 }
 
-// Fill one axis's tables in place: per-stage twiddles [n1][j-1] and the
+// Fill one axis's tables in place: per-stage twiddles [j-1][n1] and the
 // multiplier g and 1 - g at the digit-reversed positions of the forward
 // network.  Same definitions as the tables the handle-based calls build on
 // the host, computed here with the device math library.
@@ -55,8 +55,8 @@ __global__ void k_noalloc_tables(Plan pl, int N, int ntw, double tau, typename V
         const int cnt = s.m > 1 ? s.m * (s.rad - 1) : 0;
         if (i >= s.tw && i < s.tw + cnt) {
           const int loc = i - s.tw;
-          const int n1 = loc / (s.rad - 1);
-          const int j = loc - n1 * (s.rad - 1) + 1;
+          const int j = loc / s.m + 1;
+          const int n1 = loc - (j - 1) * s.m;
           const long long e = ((long long)n1 * j) % s.lb;
           double sn, cs;
           sincospi(2.0 * (double)e / (double)s.lb, &sn, &cs);

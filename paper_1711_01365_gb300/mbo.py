@@ -44,7 +44,8 @@ class MboError(RuntimeError):
 
 
 class mbo_config(C.Structure):
-    _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int)]
+    _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int),
+                ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int)]
 
 
 class mbo_stats(C.Structure):
