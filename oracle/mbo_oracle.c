@@ -385,6 +385,124 @@ int orc_project_field(const double* At, double* B, int8_t* det_sign, int64_t P, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* One step at sampled grid points, straight from the definition (Sec. 5.1):  */
+/* A~(x) = sum_y K(x - y) A(y), K the discrete periodic heat kernel, i.e. the  */
+/* inverse DFT of g; K is separable, K = K_z (x) K_y (x) K_x with             */
+/* K_a(d) = (1/N_a) sum_k exp(-4 pi^2 tau k^2) cos(2 pi k d / N_a).           */
+/* Each 1-D kernel is truncated to |d| <= r_a beyond which the Gaussian decay */
+/* of K_a puts every dropped term below 1e-22 of K_a(0).  With project_input   */
+/* the input is first projected point by point (Lemma 1.1), so the result is   */
+/* one step of Algorithm 1 from the projected field.                          */
+/* ------------------------------------------------------------------------- */
+
+static void kernel_1d(int64_t N, double tau, double* K, int64_t* radius) {
+  for (int64_t d = 0; d < N; ++d) {
+    ksum s = {0, 0};
+    for (int64_t k = 0; k < N; ++k) {
+      double kf = signed_freq(k, N);
+      ks_add(&s, exp(-4.0 * ORC_PI * ORC_PI * tau * kf * kf) * creal(root_of_unity(k * d, N, 1)));
+    }
+    K[d] = ks_val(&s) / (double)N;
+  }
+  /* The kernel is the periodised Gaussian of variance 2 tau (grid units:
+   * 2 tau N^2), so K(d) / K(0) ~ exp(-d^2 / (4 tau N^2)).  Values computed
+   * by the sum above bottom out at rounding (~1e-17 absolute), so the radius
+   * comes from that decay: dropped terms are below 1e-22 of K(0). */
+  double rr = sqrt(4.0 * tau * (double)N * (double)N * log(1e22));
+  int64_t r = (int64_t)ceil(rr) + 1;
+  if (r > N / 2) r = N / 2;
+  *radius = r;
+}
+
+static int step_points_impl(const double* A, const float* Af, int ndim, const int64_t* dims,
+                            int n, double tau, int project_input, const int64_t* pts,
+                            int64_t npts, double* At_out, double* B_out) {
+  if (ndim < 1 || ndim > 3 || n < 1 || n > ORC_MAXN) return 1;
+  int64_t d3[3] = {1, 1, 1};
+  for (int a = 0; a < ndim; ++a) d3[3 - ndim + a] = dims[a];
+  int64_t P = d3[0] * d3[1] * d3[2];
+  int C = n * n;
+  double* K[3];
+  int64_t lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t r;
+    K[a] = (double*)malloc(sizeof(double) * (size_t)d3[a]);
+    kernel_1d(d3[a], tau, K[a], &r);
+    if (d3[a] == 1) { K[a][0] = 1.0; r = 0; }
+    /* offsets -lo..hi visit every residue at most once */
+    lo[a] = r < (d3[a] - 1) / 2 ? r : (d3[a] - 1) / 2;
+    hi[a] = r < d3[a] / 2 ? r : d3[a] / 2;
+  }
+  const int64_t bz = lo[0] + hi[0] + 1, by = lo[1] + hi[1] + 1, bx = lo[2] + hi[2] + 1;
+#pragma omp parallel for schedule(dynamic)
+  for (int64_t s = 0; s < npts; ++s) {
+    int64_t c3[3] = {0, 0, 0};
+    for (int a = 0; a < ndim; ++a) c3[3 - ndim + a] = pts[s * ndim + a];
+    /* gather the neighbourhood x - d, d in [-lo, hi]^3 (periodic), projected if asked */
+    double* box = (double*)malloc(sizeof(double) * (size_t)(bz * by * bx * C));
+    for (int64_t iz = 0; iz < bz; ++iz) {
+      int64_t z = ((c3[0] - (iz - lo[0])) % d3[0] + d3[0]) % d3[0];
+      for (int64_t iy = 0; iy < by; ++iy) {
+        int64_t y = ((c3[1] - (iy - lo[1])) % d3[1] + d3[1]) % d3[1];
+        for (int64_t ix = 0; ix < bx; ++ix) {
+          int64_t x = ((c3[2] - (ix - lo[2])) % d3[2] + d3[2]) % d3[2];
+          int64_t f = (z * d3[1] + y) * d3[2] + x;
+          double* M = box + ((iz * by + iy) * bx + ix) * C;
+          for (int c = 0; c < C; ++c) M[c] = A ? A[c * P + f] : (double)Af[c * P + f];
+          if (project_input) {
+            double Bq[ORC_MAXN * ORC_MAXN];
+            orc_polar(M, Bq, NULL, n);
+            for (int c = 0; c < C; ++c) M[c] = Bq[c];
+          }
+        }
+      }
+    }
+    /* weighted sum K_z(dz) K_y(dy) K_x(dx) A(x - d), compensated */
+    double acc[ORC_MAXN * ORC_MAXN];
+    ksum ks[ORC_MAXN * ORC_MAXN];
+    for (int c = 0; c < C; ++c) ks[c].s = ks[c].c = 0;
+    for (int64_t iz = 0; iz < bz; ++iz) {
+      int64_t dz = iz - lo[0];
+      double kz = K[0][(dz % d3[0] + d3[0]) % d3[0]];
+      for (int64_t iy = 0; iy < by; ++iy) {
+        int64_t dy = iy - lo[1];
+        double kzy = kz * K[1][(dy % d3[1] + d3[1]) % d3[1]];
+        for (int64_t ix = 0; ix < bx; ++ix) {
+          int64_t dx = ix - lo[2];
+          double w = kzy * K[2][(dx % d3[2] + d3[2]) % d3[2]];
+          const double* M = box + ((iz * by + iy) * bx + ix) * C;
+          for (int c = 0; c < C; ++c) ks_add(&ks[c], w * M[c]);
+        }
+      }
+    }
+    free(box);
+    for (int c = 0; c < C; ++c) acc[c] = ks_val(&ks[c]);
+    if (At_out)
+      for (int c = 0; c < C; ++c) At_out[s * C + c] = acc[c];
+    if (B_out) {
+      double Bp[ORC_MAXN * ORC_MAXN];
+      orc_polar(acc, Bp, NULL, n);
+      for (int c = 0; c < C; ++c) B_out[s * C + c] = Bp[c];
+    }
+  }
+  for (int a = 0; a < 3; ++a) free(K[a]);
+  return 0;
+}
+
+int orc_step_points(const double* A, int ndim, const int64_t* dims, int n, double tau,
+                    int project_input, const int64_t* pts, int64_t npts, double* At_out,
+                    double* B_out) {
+  return step_points_impl(A, NULL, ndim, dims, n, tau, project_input, pts, npts, At_out, B_out);
+}
+
+/* Same, reading a float32 field (each value converted exactly to double). */
+int orc_step_points_f32(const float* A, int ndim, const int64_t* dims, int n, double tau,
+                        int project_input, const int64_t* pts, int64_t npts, double* At_out,
+                        double* B_out) {
+  return step_points_impl(NULL, A, ndim, dims, n, tau, project_input, pts, npts, At_out, B_out);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Lyapunov functional (Sec. 4 and its grid sum in Sec. 4.1)                 */
 /* ------------------------------------------------------------------------- */
 

@@ -65,8 +65,13 @@ def _load():
     lib.orc_step.argtypes = [dp, C.c_int, i64p, C.c_int, C.c_double, C.c_void_p]
     lib.orc_run.argtypes = [dp, C.c_int, i64p, C.c_int, C.c_double, C.c_int, C.c_double,
                             C.POINTER(C.c_int), C.POINTER(C.c_int), dp, dp, i64p]
+    lib.orc_step_points.argtypes = [dp, C.c_int, i64p, C.c_int, C.c_double, C.c_int, i64p,
+                                    C.c_int64, dp, dp]
+    lib.orc_step_points_f32.argtypes = [C.POINTER(C.c_float), C.c_int, i64p, C.c_int, C.c_double,
+                                        C.c_int, i64p, C.c_int64, dp, dp]
     for f in ("orc_fft", "orc_dft_direct", "orc_fftn", "orc_heat_multiplier", "orc_diffuse",
-              "orc_project_field", "orc_step", "orc_run"):
+              "orc_project_field", "orc_step", "orc_run", "orc_step_points",
+              "orc_step_points_f32"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -189,6 +194,28 @@ def step(A: np.ndarray, n: int, tau: float):
            "step")
     return A, {"energy": st.energy, "max_delta": st.max_delta, "det_flips": st.det_flips,
                "max_imag": st.max_imag}
+
+
+def step_points(A: np.ndarray, n: int, tau: float, pts, project_input: bool = False):
+    """One step evaluated only at the grid points pts (array (npts, ndim) of
+    indices), from the convolution definition of the diffusion; with
+    project_input the raw field A is projected first.  Returns (A~, B) at the
+    points, each of shape (npts, n*n)."""
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    npts = pts.shape[0]
+    At = np.empty((npts, n * n))
+    B = np.empty((npts, n * n))
+    pp = pts.ctypes.data_as(C.POINTER(C.c_int64))
+    if isinstance(A, np.ndarray) and A.dtype == np.float32 and A.flags.c_contiguous:
+        rc = _load().orc_step_points_f32(A.ctypes.data_as(C.POINTER(C.c_float)), A.ndim - 1,
+                                         _dims(A.shape[1:]), n, float(tau),
+                                         1 if project_input else 0, pp, npts, _dp(At), _dp(B))
+    else:
+        A = _f64(A)
+        rc = _load().orc_step_points(_dp(A), A.ndim - 1, _dims(A.shape[1:]), n, float(tau),
+                                     1 if project_input else 0, pp, npts, _dp(At), _dp(B))
+    _check(rc, "step_points")
+    return At, B
 
 
 def run(A: np.ndarray, n: int, tau: float, max_steps: int, tol: float):

@@ -120,7 +120,9 @@ struct mbo_ctx {
   void* W = nullptr;
   void* tabs = nullptr;  // twiddles, multipliers (one allocation)
   size_t tabs_bytes = 0;
-  double* part = nullptr;
+  double* part = nullptr;     // per-block partials, then per-group totals
+  unsigned int* cnt = nullptr;  // per-group arrival counters + the group counter
+  size_t ngroups = 0;
   RunState* st = nullptr;
   Hist hist{};
   void* hist_mem = nullptr;
@@ -247,7 +249,10 @@ StatsPtrs stats_ptrs(mbo_ctx* h, bool stats, bool respect_stop, double tol) {
   StatsPtrs sp{};
   sp.st = h->st;
   sp.hist = h->hist;
-  sp.part = h->part;
+  sp.rb.part = h->part;
+  sp.rb.gpart = h->part + h->ngroups * kReduceGroup;
+  sp.rb.gcount = h->cnt;
+  sp.rb.done = h->cnt + h->ngroups;
   sp.respect_stop = respect_stop ? 1 : 0;
   sp.do_stats = stats ? 1 : 0;
   sp.tol = tol;
@@ -392,6 +397,7 @@ mbo_status mbo_destroy(mbo_handle h) {
   cudaFree(h->W);
   cudaFree(h->tabs);
   cudaFree(h->part);
+  cudaFree(h->cnt);
   cudaFree(h->st);
   cudaFree(h->hist_mem);
   cudaFree(h->field);
@@ -481,7 +487,10 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   const int rows = g.nz * g.ny;
   const int tiles = g.Q * std::max(g.nz, g.ny) * (g.nx / h->tx);
   const size_t nparts = (size_t)std::max(rows, tiles);
-  if (!alloc(&h->W, wbytes) || !alloc((void**)&h->part, nparts * sizeof(double)) ||
+  h->ngroups = (nparts + kReduceGroup - 1) / kReduceGroup;
+  if (!alloc(&h->W, wbytes) ||
+      !alloc((void**)&h->part, (h->ngroups * kReduceGroup + h->ngroups) * sizeof(double)) ||
+      !alloc((void**)&h->cnt, (h->ngroups + 1) * sizeof(unsigned int)) ||
       !alloc((void**)&h->st, sizeof(RunState)) ||
       !alloc(&h->hist_mem, (size_t)kRing * 5 * sizeof(double))) {
     mbo_destroy(h);
@@ -507,6 +516,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     bind_tables(h, tb, h->td);
   }
   if (cudaMemset(h->st, 0, sizeof(RunState)) != cudaSuccess ||
+      cudaMemset(h->cnt, 0, (h->ngroups + 1) * sizeof(unsigned int)) != cudaSuccess ||
       cudaMemset(h->hist_mem, 0, (size_t)kRing * 5 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_st, sizeof(RunState)) != cudaSuccess ||
       cudaMallocHost(&h->h_hist, (size_t)kRing * 5 * sizeof(double)) != cudaSuccess ||

@@ -575,14 +575,15 @@ template <typename T> __device__ T block_max(T v, T* red) {
   return r;
 }
 
-// Last-block-done pattern: returns true in exactly one block (the last to
-// arrive), after all blocks' earlier global writes are visible to it.
-__device__ __forceinline__ bool last_block_arrives(unsigned int* counter, int* s_flag) {
+// Arrival counter: returns true in exactly one of `expected` arriving blocks
+// (the last), after all of their earlier global writes are visible to it.
+__device__ __forceinline__ bool last_to_arrive(unsigned int* counter, unsigned int expected,
+                                               int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
-    *s_flag = (prev == gridDim.x * gridDim.y * gridDim.z - 1) ? 1 : 0;
+    *s_flag = (prev == expected - 1) ? 1 : 0;
   }
   __syncthreads();
   const bool last = *s_flag != 0;
@@ -595,6 +596,34 @@ __device__ __forceinline__ double sum_partials(const double* p, int count, doubl
   double acc = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) acc += __ldcg(&p[i]);
   return block_sum(acc, red);
+}
+
+// Deterministic grid-wide sum of one double per block (thread 0's v), in two
+// levels: blocks are grouped by kReduceGroup consecutive indices; the last
+// block of a group to finish sums that group's partials in index order, and
+// the last group to finish sums the group totals in index order.  Returns
+// true in exactly one block, whose thread 0 receives the total.  The
+// counters return to zero.
+__device__ __forceinline__ bool grid_sum(double v, const ReduceBufs& rb, double* red, int* s_flag,
+                                         double* total) {
+  const unsigned nb = gridDim.x, b = blockIdx.x;
+  const unsigned grp = b / kReduceGroup;
+  const unsigned ngroups = (nb + kReduceGroup - 1) / kReduceGroup;
+  const unsigned gsize = min((unsigned)kReduceGroup, nb - grp * kReduceGroup);
+  if (threadIdx.x == 0) rb.part[b] = v;
+  if (!last_to_arrive(&rb.gcount[grp], gsize, s_flag)) return false;
+  const double gs = sum_partials(rb.part + grp * kReduceGroup, (int)gsize, red);
+  if (threadIdx.x == 0) {
+    rb.gpart[grp] = gs;
+    rb.gcount[grp] = 0;
+  }
+  if (!last_to_arrive(rb.done, ngroups, s_flag)) return false;
+  const double t = sum_partials(rb.gpart, (int)ngroups, red);
+  if (threadIdx.x == 0) {
+    *total = t;
+    *rb.done = 0;
+  }
+  return true;
 }
 
 }  // namespace mbo

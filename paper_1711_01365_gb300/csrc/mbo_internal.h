@@ -49,9 +49,7 @@ struct RunState {
   double energy_last;  // last energy written by a transform pass
   long long step;      // steps completed in this run
   int stop;            // 1 once a stationary step was seen (run loop only)
-  unsigned int done_axis;  // last-block counters
-  unsigned int done_row;
-  unsigned int pad_;
+  unsigned int pad_[3];
 };
 
 // Step-record ring, indexed by step & (kRing - 1).
@@ -87,10 +85,19 @@ enum AxisMode { AXIS_FWD = 0, AXIS_INV = 1, AXIS_FGI = 2, AXIS_ENERGY = 3 };
 // Modes of the row (x-axis) kernel.
 enum RowMode { ROW_FWD = 0, ROW_INV_OUT = 1, ROW_INV_PROJECT_FWD = 2 };
 
+// Buffers of the deterministic two-level grid sum (see grid_sum).
+constexpr int kReduceGroup = 256;
+struct ReduceBufs {
+  double* part;          // one partial per block
+  double* gpart;         // one total per group of kReduceGroup blocks
+  unsigned int* gcount;  // arrivals per group (zero between launches)
+  unsigned int* done;    // groups finished (zero between launches)
+};
+
 struct StatsPtrs {
   RunState* st;
   Hist hist;
-  double* part;        // per-block partial sums
+  ReduceBufs rb;       // per-block partial sums
   int respect_stop;    // 1: return at once if st->stop is set
   int do_stats;        // 1: accumulate and finalise statistics
   double tol;          // stationarity tolerance (< 0: never stop)

@@ -134,14 +134,8 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
       for (int x = tid; x < nx; x += T) W[q * P + off + x] = s[lay.addr(q, x)];
     if (sp.do_stats) {
       const double tot = block_sum((double)defect, redd);
-      if (tid == 0) sp.part[blockIdx.x] = tot;
-      if (last_block_arrives(&sp.st->done_row, &s_flag)) {
-        const double all = sum_partials(sp.part, gridDim.x, redd);
-        if (tid == 0) {
-          sp.st->defect = all;
-          sp.st->done_row = 0;
-        }
-      }
+      double all;
+      if (grid_sum(tot, sp.rb, redd, &s_flag, &all) && tid == 0) sp.st->defect = all;
     }
     return;
   }
@@ -231,14 +225,13 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
   const int nfin = block_sum(ps.nonfinite, redi);
   const int nfb = block_sum(ps.fallback, redi);
   if (tid == 0) {
-    sp.part[blockIdx.x] = dsum;
     atomicMax(&sp.st->maxdelta_bits, (unsigned long long)__double_as_longlong(mx));
     if (fl) atomicAdd(&sp.st->flips, (unsigned long long)fl);
     if (nfin) atomicAdd(&sp.st->nonfinite, (unsigned long long)nfin);
     if (nfb) atomicAdd(&sp.st->fallback, (unsigned long long)nfb);
   }
-  if (last_block_arrives(&sp.st->done_row, &s_flag)) {
-    const double all = sum_partials(sp.part, gridDim.x, redd);
+  double all;
+  if (grid_sum(dsum, sp.rb, redd, &s_flag, &all)) {
     if (tid == 0) {
       RunState* st = sp.st;
       st->defect = all;
@@ -257,7 +250,6 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
       st->fallback = 0;
       st->nonfinite = 0;
       st->step += 1;
-      st->done_row = 0;
     }
   }
 }
@@ -338,16 +330,14 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   }
   if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
     const double tot = block_sum((double)acc, redd);
-    if (tid == 0) sp.part[blockIdx.x] = tot;
-    if (last_block_arrives(&sp.st->done_axis, &s_flag)) {
-      const double all = sum_partials(sp.part, gridDim.x, redd);
+    double all;
+    if (grid_sum(tot, sp.rb, redd, &s_flag, &all)) {
       if (tid == 0) {
         RunState* st = sp.st;
         const double Pd = (double)g.P;
         const double E_tau = (all / Pd + st->defect) / (Pd * g.tau);
         st->energy_last = E_tau;
         sp.hist.energy[st->step & (kRing - 1)] = E_tau;
-        st->done_axis = 0;
       }
     }
   }

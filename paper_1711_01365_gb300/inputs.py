@@ -96,21 +96,20 @@ def voronoi(dims, seed: int, cells: int = 64, sd: float = 0.05, dtype=np.float64
     P = int(np.prod(shape))
     out = np.empty((9, P), dtype=dtype)
     coords = [np.arange(s) / s for s in shape]
-    # process in slabs along the first axis to bound memory
+    # nearest centre (minimum image on the unit torus), one slab of the first axis at a time
     plane = P // shape[0]
     grid_rest = np.stack(np.meshgrid(*coords[1:], indexing="ij"), -1).reshape(-1, d - 1)
+    rest_d2 = np.zeros((plane, cells))
+    for a in range(d - 1):
+        diff = np.abs(grid_rest[:, a:a + 1] - centres[None, :, a + 1])
+        diff = np.minimum(diff, 1.0 - diff)
+        rest_d2 += diff * diff
+    flat = rots.reshape(cells, 9)
     for i0 in range(shape[0]):
-        pts = np.concatenate([np.full((plane, 1), coords[0][i0]), grid_rest], axis=1)
-        best = np.full(plane, np.inf)
-        lab = np.zeros(plane, dtype=np.int64)
-        for c in range(cells):
-            diff = np.abs(pts - centres[c])
-            diff = np.minimum(diff, 1.0 - diff)  # minimum image on the unit torus
-            dist = (diff * diff).sum(1)
-            m = dist < best
-            best[m] = dist[m]
-            lab[m] = c
-        out[:, i0 * plane:(i0 + 1) * plane] = rots[lab].reshape(plane, 9).T
+        dz = np.abs(coords[0][i0] - centres[:, 0])
+        dz = np.minimum(dz, 1.0 - dz)
+        lab = np.argmin(rest_d2 + (dz * dz)[None, :], axis=1)
+        out[:, i0 * plane:(i0 + 1) * plane] = flat[lab].T
     out += sd * g.standard_normal(out.shape)
     return out.reshape((9,) + shape)
 
@@ -118,39 +117,52 @@ def voronoi(dims, seed: int, cells: int = 64, sd: float = 0.05, dtype=np.float64
 def smooth_so3(dims, seed: int, kc: float = 32.0, frac_reflect: float = 0.2,
                dtype=np.float32) -> np.ndarray:
     """exp([w]_x) of a smooth Gaussian so(3) field; a Bernoulli(frac) mask of
-    points is replaced by -Q, Q Haar in SO(3) (n = 3, any d)."""
+    points is replaced by -Q, Q Haar in SO(3) (n = 3, any d).
+
+    Each component of w is white noise filtered by sqrt(exp(-|k|^2 / kc^2)) (k
+    in integer cycles over the unit torus) and normalised to unit pointwise
+    standard deviation.  Computed in float32 with scipy.fft (all cores)."""
+    import scipy.fft as sfft
     g = rng(seed)
     shape = tuple(int(s) for s in dims)
     P = int(np.prod(shape))
-    ks = np.meshgrid(*[np.fft.fftfreq(s, 1.0 / s) for s in shape], indexing="ij", sparse=True)
-    k2 = sum(k.astype(np.float64) ** 2 for k in ks)
-    amp = np.sqrt(np.exp(-k2 / kc ** 2))
-    w = np.empty((3, P), dtype=np.float64)
+    freqs = [np.fft.fftfreq(s, 1.0 / s) for s in shape[:-1]] + [np.fft.rfftfreq(shape[-1], 1.0 / shape[-1])]
+    amp = np.ones([len(f) for f in freqs], dtype=np.float32)
+    for ax, f in enumerate(freqs):
+        sh = [1] * len(shape)
+        sh[ax] = len(f)
+        amp = amp * np.exp(-(f.astype(np.float64) ** 2) / (2 * kc ** 2)).astype(np.float32).reshape(sh)
+    w = np.empty((3, P), dtype=np.float32)
     for i in range(3):
-        white = g.standard_normal(shape)
-        f = np.fft.ifftn(np.fft.fftn(white) * amp).real
+        white = g.standard_normal(shape, dtype=np.float32)
+        f = sfft.irfftn(sfft.rfftn(white, workers=-1) * amp, s=shape, workers=-1)
         f /= f.std()
         w[i] = f.reshape(-1)
+        del white, f
     theta = np.sqrt((w * w).sum(0))
-    safe = np.where(theta > 0, theta, 1.0)
-    kx, ky, kz = w / safe
-    s, c1 = np.sin(theta), 1.0 - np.cos(theta)
-    R = np.empty((9, P), dtype=np.float64)
+    safe = np.where(theta > 0, theta, 1.0).astype(np.float32)
+    w /= safe
+    kx, ky, kz = w
+    s = np.sin(theta)
+    c1 = (1.0 - np.cos(theta)).astype(np.float32)
+    del theta, safe
+    R = np.empty((9, P), dtype=dtype)
     # Rodrigues: I + sin(t) K + (1 - cos(t)) K^2 for the unit axis (kx, ky, kz)
-    R[0] = 1 + c1 * (-(ky * ky + kz * kz))
+    R[0] = 1 - c1 * (ky * ky + kz * kz)
     R[1] = -s * kz + c1 * kx * ky
     R[2] = s * ky + c1 * kx * kz
     R[3] = s * kz + c1 * kx * ky
-    R[4] = 1 + c1 * (-(kx * kx + kz * kz))
+    R[4] = 1 - c1 * (kx * kx + kz * kz)
     R[5] = -s * kx + c1 * ky * kz
     R[6] = -s * ky + c1 * kx * kz
     R[7] = s * kx + c1 * ky * kz
-    R[8] = 1 + c1 * (-(kx * kx + ky * ky))
+    R[8] = 1 - c1 * (kx * kx + ky * ky)
+    del w, s, c1
     mask = g.random(P) < frac_reflect
     cnt = int(mask.sum())
     if cnt:
-        R[:, mask] = -haar_so3(cnt, g).reshape(cnt, 9).T
-    return R.astype(dtype).reshape((9,) + shape)
+        R[:, mask] = (-haar_so3(cnt, g).reshape(cnt, 9).T).astype(dtype)
+    return R.reshape((9,) + shape)
 
 
 # Batched 2-D workload: field i gets N = SIZES[i % 7], n = 2 + (i % 2), tau = 4 / N^2.
@@ -177,9 +189,11 @@ CONFIGS = {
 }
 
 
-def config_field(name: str, seed: int | None = None, dims=None) -> tuple[np.ndarray, int, float]:
+def config_field(name: str, seed: int | None = None, dims=None,
+                 dtype=np.float64) -> tuple[np.ndarray, int, float]:
     """Raw initial field for a named workload, optionally at smaller dims
-    (tau is rescaled to keep the same multiple of h^2)."""
+    (tau is rescaled to keep the same multiple of h^2).  dtype applies to the
+    3-D recipes (float32 halves the host memory of the 512^3 field)."""
     cfg = CONFIGS[name]
     seed = SEED_BASE + int(name[1:]) if seed is None else seed
     d = tuple(dims) if dims is not None else cfg["dims"]
@@ -191,9 +205,9 @@ def config_field(name: str, seed: int | None = None, dims=None) -> tuple[np.ndar
     elif init == "sign_split":
         F = sign_split(d, n, seed)
     elif init == "voronoi":
-        F = voronoi(d, seed)
+        F = voronoi(d, seed, dtype=dtype)
     elif init == "smooth_so3":
-        F = smooth_so3(d, seed, kc=32.0 * d[-1] / cfg["dims"][-1], dtype=np.float64)
+        F = smooth_so3(d, seed, kc=32.0 * d[-1] / cfg["dims"][-1], dtype=dtype)
     else:
         raise ValueError(init)
     return F, n, tau

@@ -1,0 +1,121 @@
+"""Parity at the full sizes of the benchmark configurations, in the launch
+configuration the benchmark uses (default mbo_config).
+
+  * 1024 x 1024, n = 3, tau = 3h^2 (sign-split start): one step from the
+    oracle's own projection of the raw field, FP64 and FP32 forms, every point
+    compared with the full oracle step, energies compared.
+  * 256^3, n = 3, tau = 2h^2 (Voronoi rotations + noise) and 512^3, n = 3,
+    tau = 2h^2 (smooth SO(3) field with 20% reflections), FP32 form with FP64
+    re-projection: the library projects the raw field and takes one step; the
+    oracle computes the same step at sampled points one by one from the raw
+    field (its own projection, the convolution with the periodic heat kernel,
+    its own projection).  Properties that hold at any size are checked on every
+    point: orthogonality, and an energy that does not increase over steps.
+
+Tolerances are those of test_gpu_parity (max-entry 1e-12 in FP64; in FP32
+2e-5 where sigma_{n-1} + sigma_n >= 0.1, else the condition-number bound).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1711_01365_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_STEP_TOL = 2e-5
+F32_DIFF_TOL = 4e-6
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1711_01365_gb300 import build
+    build.build()
+    from paper_1711_01365_gb300 import mbo
+    return mbo
+
+
+def _sv(At, n):
+    return np.linalg.svd(At.reshape(-1, n, n), compute_uv=False)
+
+
+def _orth_defect_gpu(A, n):
+    """max over points of max |(B^t B - I)_ij| for a (n*n, ...) device field."""
+    B = A.reshape(n, n, -1).double()
+    G = torch.einsum("kip,kjp->ijp", B, B)
+    G -= torch.eye(n, dtype=G.dtype, device=G.device)[:, :, None]
+    return G.abs().max().item()
+
+
+def test_c2_full_field_one_step_matches_oracle(M):
+    F, n, tau = I.config_field("C2")
+    dims = F.shape[1:]
+    A0 = O.project(F, n)
+    ref, st = O.step(A0, n, tau)
+    At = O.diffuse(A0, tau)
+    s = _sv(np.moveaxis(At.reshape(n * n, -1), 0, -1), n)
+    cs = (s[:, -1] + s[:, -2]).reshape(dims)
+    absdet = np.abs(np.prod(s, axis=1)).reshape(dims)
+    for dtype in ("f64", "f32"):
+        h = M.Mbo(dims, n, tau, dtype)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        a = torch.tensor(A0, dtype=tdt, device="cuda")
+        rec = h.step(a, want_stats=True)
+        B = a.double().cpu().numpy()
+        err = np.abs(B - ref).max(axis=0)
+        if dtype == "f64":
+            unamb = absdet > 1e-12
+            assert err[unamb].max() <= 1e-12
+            assert rec["energy"] == pytest.approx(st["energy"], rel=1e-12)
+        else:
+            unamb = absdet > 1e-4
+            well = unamb & (cs >= 0.1)
+            assert err[well].max() <= F32_STEP_TOL
+            bound = F32_STEP_TOL + 2 * n * F32_DIFF_TOL / np.maximum(cs, 1e-30)
+            assert np.all(err[unamb] <= bound[unamb])
+            assert rec["energy"] == pytest.approx(st["energy"], rel=1e-5)
+        assert _orth_defect_gpu(a, n) < (1e-13 if dtype == "f64" else 2e-6)
+        h.close()
+
+
+def _sampled_3d_case(M, name, nsamples, seed):
+    F, n, tau = I.config_field(name, dtype=np.float32)
+    dims = F.shape[1:]
+    h = M.Mbo(dims, n, tau, "f32")
+    raw = torch.from_numpy(F).cuda()
+    A = torch.empty_like(raw)
+    h.project(raw, A)
+    del raw
+    torch.cuda.synchronize()
+    g = I.rng(seed)
+    pts = np.stack([g.integers(0, d, nsamples) for d in dims], 1)
+    At_o, B_o = O.step_points(F, n, tau, pts, project_input=True)
+    rec = h.step(A, want_stats=True)
+    idx = (slice(None),) + tuple(torch.as_tensor(pts.T))
+    B = A[idx].double().cpu().numpy().T  # (nsamples, 9)
+    s = _sv(At_o, n)
+    cs = s[:, -1] + s[:, -2]
+    absdet = np.prod(s, axis=1)
+    err = np.abs(B - B_o).max(axis=1)
+    unamb = absdet > 1e-4
+    well = unamb & (cs >= 0.1)
+    assert well.sum() >= nsamples // 2
+    assert err[well].max() <= F32_STEP_TOL
+    bound = F32_STEP_TOL + 2 * n * F32_DIFF_TOL / np.maximum(cs, 1e-30)
+    assert np.all(err[unamb] <= bound[unamb])
+    assert rec["nonfinite"] == 0
+    assert _orth_defect_gpu(A, n) < 2e-6
+    energies = [rec["energy"]]
+    for _ in range(3):
+        energies.append(h.step(A, flags=M.MBO_STEP_CONTINUE, want_stats=True)["energy"])
+    assert all(e2 <= e1 * (1 + 1e-6) for e1, e2 in zip(energies, energies[1:]))
+    h.close()
+
+
+def test_c3_256cube_one_step_sampled_against_oracle(M):
+    _sampled_3d_case(M, "C3", 96, 31)
+
+
+def test_c5_512cube_one_step_sampled_against_oracle(M):
+    _sampled_3d_case(M, "C5", 64, 53)

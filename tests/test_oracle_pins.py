@@ -414,3 +414,22 @@ def test_input_generators_are_seeded_and_shaped():
     R = I.haar_so3(20, I.rng(1))
     assert np.allclose(np.einsum("kij,kil->kjl", R, R), np.eye(3)[None], atol=1e-12)
     assert np.allclose(np.linalg.det(R), 1.0)
+
+
+@pytest.mark.parametrize("dims,n", [((24, 32), 3), ((8, 12, 16), 2), ((9, 27), 1), ((64, 64), 3)])
+def test_step_at_points_matches_full_step(dims, n):
+    """The convolution-definition step at sampled points (used at sizes where the
+    full oracle step is too slow) equals the spectral full step, from float64
+    and from float32 raw input."""
+    F = I.gaussian(dims, n, 3)
+    tau = 3.0 / max(dims) ** 2
+    g = I.rng(1)
+    pts = np.stack([g.integers(0, d, 25) for d in dims], 1)
+    idx = (slice(None),) + tuple(pts.T)
+    for raw in (F, F.astype(np.float32)):
+        A0 = O.project(raw.astype(np.float64), n)
+        At = O.diffuse(A0, tau)
+        B = O.project(At, n)
+        At_p, B_p = O.step_points(raw, n, tau, pts, project_input=True)
+        assert np.abs(At_p - At[idx].T).max() < 1e-14
+        assert np.abs(B_p - B[idx].T).max() < 1e-12
