@@ -199,6 +199,47 @@ MBO_API mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, dou
                                        mbo_dtype dtype, const void* A, void* A_tilde,
                                        void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batches of independent fields.  Fields may differ in ndim, dims, n and tau */
+/* (one dtype per batch).  One step of the batch runs every field's step     */
+/* (Algorithm 1) from a single CUDA graph launch whose per-field branches are */
+/* independent, so fields of uneven sizes run concurrently.                  */
+/* ------------------------------------------------------------------------- */
+typedef struct mbo_batch_ctx* mbo_batch;
+
+/* count fields; field i has ndim[i] in {2, 3} and dims dims[3*i .. 3*i+ndim[i]-1]
+ * (as in mbo_create), order n[i] and diffusion time tau[i].  Allocates each
+ * field's workspace and tables.  Synchronous.  Errors as mbo_create (the
+ * first failing field is named by mbo_batch_last_error). */
+MBO_API mbo_status mbo_batch_create(mbo_batch* out, int count, const int* ndim, const int64_t* dims,
+                                    const int* n, const double* tau, mbo_dtype dtype,
+                                    const mbo_config* cfg);
+MBO_API mbo_status mbo_batch_destroy(mbo_batch b);
+
+/* One step of every field, in place: A[i] is field i's caller-owned device
+ * field (layout as in mbo_step).  flags: MBO_STEP_CONTINUE as in mbo_step.
+ * stats (nullable, count records): if given the call synchronises and fills
+ * each field's record.  The step graph is captured on first use for a set of
+ * field pointers and replayed afterwards. */
+MBO_API mbo_status mbo_batch_step(mbo_batch b, void* const* A, int flags, mbo_stats* stats,
+                                  void* stream);
+
+/* Iterate every field until its own step is stationary (then its kernels
+ * skip further steps) or max_steps steps were taken, as
+ * mbo_run_until_stationary.  A[i]: device fields.  Outputs (nullable):
+ * steps_taken[count], stationary[count], energies[count * (max_steps + 1)]
+ * (row i: E^tau(A_0) .. E^tau(A_steps_i) of field i), last[count].
+ * Synchronises the stream before returning. */
+MBO_API mbo_status mbo_batch_run(mbo_batch b, void* const* A, int max_steps, double tol,
+                                 int* steps_taken, int* stationary, double* energies,
+                                 mbo_stats* last, void* stream);
+
+/* Total device bytes the batch holds. */
+MBO_API int64_t mbo_batch_workspace_bytes(mbo_batch b);
+
+/* Text of the last error recorded in the batch. */
+MBO_API const char* mbo_batch_last_error(mbo_batch b);
+
 /* Bytes of device memory the handle holds (workspace and tables). */
 MBO_API int64_t mbo_workspace_bytes(mbo_handle h);
 

@@ -515,6 +515,12 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     cudaMemcpy(h->tabs, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice);
     bind_tables(h, tb, h->td);
   }
+  const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tx)
+                                          : prepare_kernels<double>(g, h->tx);
+  if (pe != cudaSuccess) {
+    mbo_destroy(h);
+    return MBO_ERR_CUDA;
+  }
   if (cudaMemset(h->st, 0, sizeof(RunState)) != cudaSuccess ||
       cudaMemset(h->cnt, 0, (h->ngroups + 1) * sizeof(unsigned int)) != cudaSuccess ||
       cudaMemset(h->hist_mem, 0, (size_t)kRing * 5 * sizeof(double)) != cudaSuccess ||
@@ -767,6 +773,272 @@ mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npa
     if (ms) ms[i] = h->prof_ms[i];
     if (launches) launches[i] = h->prof_n[i];
   }
+  return MBO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent fields (uneven sizes and orders).  Each field keeps
+// its own single-field context; one step of the whole batch is one CUDA graph
+// whose per-field branches (spread over worker streams) are independent, so
+// fields of different sizes run concurrently and the host launches once per
+// step.
+// ---------------------------------------------------------------------------
+
+struct mbo_batch_ctx {
+  int dev = 0;
+  int count = 0;
+  mbo_config cfg{};
+  std::vector<mbo_ctx*> f;
+  std::vector<cudaStream_t> ws;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> g_ptrs;
+  double g_tol = 0;
+  int g_run = -1;
+  char err[512] = {0};
+};
+
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+mbo_status bfail(mbo_batch_ctx* b, mbo_status s, const char* what, cudaError_t e) {
+  if (b) snprintf(b->err, sizeof(b->err), "%s: %s", what, cudaGetErrorString(e));
+  return s;
+}
+
+#define BCK(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? MBO_ERR_OOM : MBO_ERR_CUDA, #call, e_); \
+  } while (0)
+
+// Capture one step of every field (run: stop flags respected, tol) into b->gexec.
+mbo_status batch_capture(mbo_batch_ctx* b, void* const* A, bool run, double tol) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b->fork, b->cap);
+  for (size_t k = 0; k < b->ws.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->ws[k], b->fork, 0);
+  for (int i = 0; i < b->count && e == cudaSuccess; ++i)
+    e = step_passes(b->f[i], A[i], run, run ? tol : -1.0, b->ws[i % b->ws.size()]);
+  for (size_t k = 0; k < b->ws.size() && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->join[k], b->ws[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, MBO_ERR_CUDA, "batch graph capture", e != cudaSuccess ? e : e2);
+  }
+  e = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfail(b, MBO_ERR_CUDA, "batch graph instantiate", e);
+  b->g_ptrs.assign(A, A + b->count);
+  b->g_tol = tol;
+  b->g_run = run ? 1 : 0;
+  return MBO_OK;
+}
+
+bool batch_graph_matches(const mbo_batch_ctx* b, void* const* A, bool run, double tol) {
+  if (!b->gexec || b->g_run != (run ? 1 : 0) || (run && b->g_tol != tol)) return false;
+  for (int i = 0; i < b->count; ++i)
+    if (b->g_ptrs[i] != A[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+mbo_status mbo_batch_destroy(mbo_batch h) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(h->dev);
+  cudaDeviceSynchronize();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto s : h->ws) cudaStreamDestroy(s);
+  for (auto e : h->join) cudaEventDestroy(e);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  for (auto f : h->f)
+    if (f) mbo_destroy(f);
+  delete h;
+  return MBO_OK;
+}
+
+mbo_status mbo_batch_create(mbo_batch* out, int count, const int* ndim, const int64_t* dims,
+                            const int* n, const double* tau, mbo_dtype dtype,
+                            const mbo_config* cfg) {
+  if (!out || count < 1 || !ndim || !dims || !n || !tau) return MBO_ERR_INVALID_ARG;
+  *out = nullptr;
+  mbo_batch_ctx* b = new mbo_batch_ctx();
+  b->count = count;
+  if (cfg) b->cfg = *cfg;
+  else mbo_default_config(&b->cfg);
+  cudaGetDevice(&b->dev);
+  b->f.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    mbo_status rc = mbo_create(&b->f[i], ndim[i], dims + 3 * (size_t)i, n[i], tau[i], dtype, &b->cfg);
+    if (rc != MBO_OK) {
+      snprintf(b->err, sizeof(b->err), "field %d: %s", i, mbo_status_string(rc));
+      mbo_batch_destroy(b);
+      return rc;
+    }
+  }
+  const int nws = std::min(count, kBatchStreams);
+  b->ws.assign(nws, nullptr);
+  b->join.assign(nws, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < nws && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&b->ws[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mbo_batch_destroy(b);
+    return MBO_ERR_CUDA;
+  }
+  *out = b;
+  return MBO_OK;
+}
+
+int64_t mbo_batch_workspace_bytes(mbo_batch h) {
+  if (!h) return 0;
+  int64_t t = 0;
+  for (auto f : h->f) t += mbo_workspace_bytes(f);
+  return t;
+}
+
+const char* mbo_batch_last_error(mbo_batch h) { return h ? h->err : ""; }
+
+mbo_status mbo_batch_step(mbo_batch b, void* const* A, int flags, mbo_stats* stats, void* stream) {
+  if (!b || !A) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(b->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->count; ++i) {
+    mbo_ctx* h = b->f[i];
+    mbo_status rc = check_field_ptr(h, A[i], "A[i]");
+    if (rc != MBO_OK) {
+      snprintf(b->err, sizeof(b->err), "field %d: %s", i, h->err);
+      return rc;
+    }
+    if (!((flags & MBO_STEP_CONTINUE) && h->w_valid_for == A[i]))
+      BCK(row_pass(h, ROW_FWD, A[i], nullptr, stats_ptrs(h, true, false, -1.0), s));
+  }
+  if (!batch_graph_matches(b, A, false, -1.0)) {
+    mbo_status rc = batch_capture(b, A, false, -1.0);
+    if (rc != MBO_OK) return rc;
+  }
+  BCK(cudaGraphLaunch(b->gexec, s));
+  for (int i = 0; i < b->count; ++i) b->f[i]->w_valid_for = A[i];
+  if (stats) {
+    BCK(cudaStreamSynchronize(s));
+    for (int i = 0; i < b->count; ++i) {
+      mbo_ctx* h = b->f[i];
+      BCK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+      const long long slot = (h->h_st->step - 1) & (kRing - 1);
+      mbo_status rc = read_record(h, slot, &stats[i]);
+      if (rc != MBO_OK) return rc;
+      if (stats[i].nonfinite) {
+        snprintf(b->err, sizeof(b->err), "field %d: non-finite values", i);
+        return MBO_ERR_NUMERIC;
+      }
+    }
+  }
+  return MBO_OK;
+}
+
+mbo_status mbo_batch_run(mbo_batch b, void* const* A, int max_steps, double tol, int* steps_taken,
+                         int* stationary, double* energies, mbo_stats* last, void* stream) {
+  if (!b || !A || max_steps < 0) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(b->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int C = b->count;
+  for (int i = 0; i < C; ++i) {
+    mbo_ctx* h = b->f[i];
+    mbo_status rc = check_field_ptr(h, A[i], "A[i]");
+    if (rc != MBO_OK) {
+      snprintf(b->err, sizeof(b->err), "field %d: %s", i, h->err);
+      return rc;
+    }
+    BCK(cudaMemsetAsync(h->st, 0, sizeof(RunState), s));
+    BCK(row_pass(h, ROW_FWD, A[i], nullptr, stats_ptrs(h, true, false, -1.0), s));
+  }
+  if (max_steps > 0 && !batch_graph_matches(b, A, true, tol)) {
+    mbo_status rc = batch_capture(b, A, true, tol);
+    if (rc != MBO_OK) return rc;
+  }
+  const int K = b->cfg.check_interval < 1 ? 1 : std::min(b->cfg.check_interval, kRing / 2);
+  const size_t stride = (size_t)max_steps + 1;
+  std::vector<long long> copied(C, 0), nonfinite(C, 0);
+  std::vector<int> stopped(C, 0);
+  auto harvest = [&](int i, long long upto, bool final_energy) -> mbo_status {
+    mbo_ctx* h = b->f[i];
+    BCK(cudaMemcpy(h->h_hist, h->hist_mem, (size_t)kRing * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+    const double* hh = static_cast<const double*>(h->h_hist);
+    const long long* nf = reinterpret_cast<const long long*>(hh + 4 * kRing);
+    for (long long t = copied[i]; t < upto; ++t) {
+      nonfinite[i] += nf[t & (kRing - 1)];
+      if (energies) energies[i * stride + t] = hh[t & (kRing - 1)];
+    }
+    if (final_energy && energies) energies[i * stride + upto] = hh[upto & (kRing - 1)];
+    copied[i] = upto;
+    return MBO_OK;
+  };
+  int done = 0;
+  while (done < max_steps) {
+    const int chunk = std::min(K, max_steps - done);
+    for (int k = 0; k < chunk; ++k) BCK(cudaGraphLaunch(b->gexec, s));
+    done += chunk;
+    for (int i = 0; i < C; ++i)
+      BCK(cudaMemcpyAsync(b->f[i]->h_st, b->f[i]->st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    int all = 1;
+    for (int i = 0; i < C; ++i) {
+      stopped[i] = b->f[i]->h_st->stop != 0;
+      all &= stopped[i];
+      mbo_status rc = harvest(i, b->f[i]->h_st->step, false);
+      if (rc != MBO_OK) return rc;
+    }
+    if (all) break;
+  }
+  for (int i = 0; i < C; ++i)
+    BCK(middle_passes(b->f[i], AXIS_ENERGY, stats_ptrs(b->f[i], true, false, -1.0), s));
+  BCK(cudaStreamSynchronize(s));
+  for (int i = 0; i < C; ++i) {
+    mbo_ctx* h = b->f[i];
+    BCK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+    const long long st = h->h_st->step;
+    mbo_status rc = harvest(i, st, true);
+    if (rc != MBO_OK) return rc;
+    h->w_valid_for = (h->g.ndim == 2) ? A[i] : nullptr;
+    if (steps_taken) steps_taken[i] = (int)st;
+    if (stationary) stationary[i] = stopped[i];
+    if (last) {
+      const double* hh = static_cast<const double*>(h->h_hist);
+      const long long* fl = reinterpret_cast<const long long*>(hh + 2 * kRing);
+      const long long* fb = reinterpret_cast<const long long*>(hh + 3 * kRing);
+      const long long* nf = reinterpret_cast<const long long*>(hh + 4 * kRing);
+      const long long sl = (st > 0 ? st - 1 : 0) & (kRing - 1);
+      last[i].energy = hh[sl];
+      last[i].max_delta = st > 0 ? hh[kRing + sl] : 0.0;
+      last[i].det_flips = st > 0 ? fl[sl] : 0;
+      last[i].fallback_points = st > 0 ? fb[sl] : 0;
+      last[i].nonfinite = st > 0 ? nf[sl] : 0;
+    }
+  }
+  for (int i = 0; i < C; ++i)
+    if (nonfinite[i]) {
+      snprintf(b->err, sizeof(b->err), "field %d: non-finite values during the run", i);
+      return MBO_ERR_NUMERIC;
+    }
   return MBO_OK;
 }
 

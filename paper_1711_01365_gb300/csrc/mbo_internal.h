@@ -122,6 +122,8 @@ Plan make_plan(int N);
 int plan_twiddles(const Plan& p);
 int pick_tx(int nx, int cap);
 
+template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx);
+
 // Shared memory bytes of the row kernel for a geometry.
 size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback);
 size_t axis_smem_bytes(int len, int tx, size_t elem_bytes);

@@ -375,12 +375,13 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes, size_t
 
 template <typename R, int NM, int MODE>
 static cudaError_t launch_row_nm(const Geom& g, const Tables<R>& t, const R* Ain, R* A, void* W,
-                                 const StatsPtrs& sp, R fb, int threads, cudaStream_t s) {
+                                 const StatsPtrs& sp, R fb, int threads, cudaStream_t s,
+                                 bool prepare_only = false) {
   auto k = k_row<R, NM, MODE>;
   static size_t done = 0;
   const size_t smem = row_smem_bytes(g, sizeof(R), MODE == ROW_INV_PROJECT_FWD);
   cudaError_t e = set_smem(k, smem, done);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || prepare_only) return e;
   const int rows = g.nz * g.ny;
   k<<<rows, threads, smem, s>>>(g, t, Ain, A, static_cast<typename VT<R>::V*>(W), sp, fb);
   return cudaGetLastError();
@@ -409,13 +410,14 @@ cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R*
 
 template <typename R, int MODE>
 static cudaError_t launch_axis_m(const Geom& g, const Tables<R>& t, void* W, const StatsPtrs& sp,
-                                 int axis, int tx, int threads, cudaStream_t s) {
+                                 int axis, int tx, int threads, cudaStream_t s,
+                                 bool prepare_only = false) {
   auto k = k_axis<R, MODE>;
   static size_t done = 0;
   const int L = axis == 1 ? g.ny : g.nz;
   const size_t smem = axis_smem_bytes(L, tx, sizeof(R));
   cudaError_t e = set_smem(k, smem, done);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || prepare_only) return e;
   int ltx = 0;
   while ((1 << ltx) < tx) ++ltx;
   const int nouter = axis == 1 ? g.nz : g.ny;
@@ -448,7 +450,40 @@ cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
   return cudaGetLastError();
 }
 
+// Raise the shared-memory limit of every kernel a geometry uses, without
+// launching (so that later launches inside stream capture make no attribute
+// call).
+template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx) {
+  Tables<R> t{};
+  StatsPtrs sp{};
+  cudaError_t e = cudaSuccess;
+#define MBO_PREP_ROW(NM)                                                                       \
+  if (g.n == NM) {                                                                             \
+    if (e == cudaSuccess)                                                                      \
+      e = launch_row_nm<R, NM, ROW_FWD>(g, t, nullptr, nullptr, nullptr, sp, R(0), 32, 0, true); \
+    if (e == cudaSuccess)                                                                      \
+      e = launch_row_nm<R, NM, ROW_INV_OUT>(g, t, nullptr, nullptr, nullptr, sp, R(0), 32, 0,  \
+                                            true);                                             \
+    if (e == cudaSuccess)                                                                      \
+      e = launch_row_nm<R, NM, ROW_INV_PROJECT_FWD>(g, t, nullptr, nullptr, nullptr, sp, R(0), \
+                                                    32, 0, true);                              \
+  }
+  MBO_PREP_ROW(1)
+  MBO_PREP_ROW(2)
+  MBO_PREP_ROW(3)
+#undef MBO_PREP_ROW
+  for (int axis = 1; axis <= (g.ndim == 3 ? 2 : 1) && e == cudaSuccess; ++axis) {
+    e = launch_axis_m<R, AXIS_FWD>(g, t, nullptr, sp, axis, tx, 64, 0, true);
+    if (e == cudaSuccess) e = launch_axis_m<R, AXIS_INV>(g, t, nullptr, sp, axis, tx, 64, 0, true);
+    if (e == cudaSuccess) e = launch_axis_m<R, AXIS_FGI>(g, t, nullptr, sp, axis, tx, 64, 0, true);
+    if (e == cudaSuccess)
+      e = launch_axis_m<R, AXIS_ENERGY>(g, t, nullptr, sp, axis, tx, 64, 0, true);
+  }
+  return e;
+}
+
 #define MBO_INSTANTIATE(R)                                                                     \
+  template cudaError_t prepare_kernels<R>(const Geom&, int);                                   \
   template cudaError_t launch_row<R>(RowMode, const Geom&, const Tables<R>&, const R*, R*,     \
                                      void*, const StatsPtrs&, double, int, cudaStream_t);      \
   template cudaError_t launch_axis<R>(AxisMode, int, const Geom&, const Tables<R>&, void*,     \

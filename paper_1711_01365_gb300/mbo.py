@@ -28,8 +28,9 @@ STATUS = {0: "MBO_OK", 1: "MBO_ERR_INVALID_ARG", 2: "MBO_ERR_UNSUPPORTED_SIZE", 
 
 EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project",
            "mbo_step", "mbo_lyapunov", "mbo_run_until_stationary", "mbo_profile_enable",
-           "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_workspace_bytes", "mbo_status_string",
-           "mbo_last_error")
+           "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_batch_create", "mbo_batch_destroy",
+           "mbo_batch_step", "mbo_batch_run", "mbo_batch_workspace_bytes", "mbo_batch_last_error",
+           "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
 
 MBO_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -89,6 +90,17 @@ def lib():
     L.mbo_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_diffuse_noalloc.argtypes = [C.c_int, i64p, C.c_int, C.c_double, C.c_int, vp, vp, vp]
+    L.mbo_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), i64p,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int,
+                                   C.POINTER(mbo_config)]
+    L.mbo_batch_destroy.argtypes = [vp]
+    L.mbo_batch_step.argtypes = [vp, C.POINTER(vp), C.c_int, C.POINTER(mbo_stats), vp]
+    L.mbo_batch_run.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(mbo_stats), vp]
+    L.mbo_batch_workspace_bytes.argtypes = [vp]
+    L.mbo_batch_workspace_bytes.restype = C.c_int64
+    L.mbo_batch_last_error.argtypes = [vp]
+    L.mbo_batch_last_error.restype = C.c_char_p
     L.mbo_workspace_bytes.argtypes = [vp]
     L.mbo_workspace_bytes.restype = C.c_int64
     L.mbo_status_string.argtypes = [C.c_int]
@@ -97,7 +109,8 @@ def lib():
     L.mbo_last_error.restype = C.c_char_p
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
               "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
-              "mbo_diffuse_noalloc"):
+              "mbo_diffuse_noalloc", "mbo_batch_create", "mbo_batch_destroy", "mbo_batch_step",
+              "mbo_batch_run"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -210,6 +223,95 @@ def mbo_profile_read(h) -> dict:
     cnt = (C.c_int64 * n)()
     _check(lib().mbo_profile_read(h, ms, cnt, n), h)
     return {PASSES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def _bcheck(rc: int, b) -> None:
+    if rc != 0:
+        msg = lib().mbo_status_string(rc).decode()
+        if b is not None:
+            d = lib().mbo_batch_last_error(b).decode()
+            if d:
+                msg += f" ({d})"
+        raise MboError(rc, msg)
+
+
+def mbo_batch_create(dims_list, n_list, tau_list, dtype: int = MBO_F32,
+                     cfg: mbo_config | None = None):
+    """Handle for a batch of independent fields (dims may differ per field)."""
+    cnt = len(dims_list)
+    nd = (C.c_int * cnt)(*[len(d) for d in dims_list])
+    flat = []
+    for d in dims_list:
+        flat += [int(v) for v in d] + [0] * (3 - len(d))
+    dd = (C.c_int64 * (3 * cnt))(*flat)
+    nn = (C.c_int * cnt)(*[int(v) for v in n_list])
+    tt = (C.c_double * cnt)(*[float(v) for v in tau_list])
+    b = C.c_void_p()
+    rc = lib().mbo_batch_create(C.byref(b), cnt, nd, dd, nn, tt, int(dtype),
+                                C.byref(cfg) if cfg is not None else None)
+    _bcheck(rc, None)
+    return b
+
+
+def mbo_batch_destroy(b) -> None:
+    _bcheck(lib().mbo_batch_destroy(b), None)
+
+
+def _ptrs(fields):
+    return (C.c_void_p * len(fields))(*[_ptr(f) for f in fields])
+
+
+def mbo_batch_step(b, fields, flags: int = 0, want_stats: bool = False, stream=None):
+    st = (mbo_stats * len(fields))()
+    _bcheck(lib().mbo_batch_step(b, _ptrs(fields), int(flags), st if want_stats else None,
+                                 _stream(stream)), b)
+    return [s.as_dict() for s in st] if want_stats else None
+
+
+def mbo_batch_run(b, fields, max_steps: int, tol: float, stream=None) -> dict:
+    cnt = len(fields)
+    steps = (C.c_int * cnt)()
+    stat = (C.c_int * cnt)()
+    en = np.zeros((cnt, max_steps + 1), dtype=np.float64)
+    last = (mbo_stats * cnt)()
+    _bcheck(lib().mbo_batch_run(b, _ptrs(fields), int(max_steps), float(tol), steps, stat,
+                                en.ctypes.data_as(C.POINTER(C.c_double)), last, _stream(stream)), b)
+    return {"steps": list(steps), "stationary": [bool(x) for x in stat],
+            "energies": [en[i, : steps[i] + 1] for i in range(cnt)],
+            "last": [s.as_dict() for s in last]}
+
+
+def mbo_batch_workspace_bytes(b) -> int:
+    return int(lib().mbo_batch_workspace_bytes(b))
+
+
+class Batch:
+    """Owning wrapper of a batch handle."""
+
+    def __init__(self, dims_list, n_list, tau_list, dtype: str = "f32", **cfg):
+        c = mbo_default_config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.count = len(dims_list)
+        self.b = mbo_batch_create(dims_list, n_list, tau_list,
+                                  {"f32": MBO_F32, "f64": MBO_F64}[dtype], c)
+
+    def close(self) -> None:
+        if getattr(self, "b", None) is not None:
+            mbo_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, fields, flags=0, want_stats=False, stream=None):
+        return mbo_batch_step(self.b, fields, flags, want_stats, stream)
+
+    def run(self, fields, max_steps: int, tol: float, stream=None) -> dict:
+        return mbo_batch_run(self.b, fields, max_steps, tol, stream)
 
 
 def mbo_workspace_bytes(h) -> int:
