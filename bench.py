@@ -39,6 +39,33 @@ UNIT = "grid-point iterations/s"
 WORKLOAD = "C2"
 
 
+def kernel_sources_hash() -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources, concatenated as
+    csrc/*.cu, *.cuh, *.h in name order."""
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_1711_01365_gb300", "csrc")
+    data = b""
+    for pat in ("*.cu", "*.cuh", "*.h"):
+        for f in sorted(glob.glob(os.path.join(d, pat))):
+            with open(f, "rb") as fh:
+                data += fh.read()
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the last ncu capture, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("sources_sha256_16") != kernel_sources_hash() or kernel not in rec.get("kernel", ""):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -306,9 +333,10 @@ def run_ours(args, ws, rank, local):
     ax_t = ax_ms / 1e3 / max(ax_n, 1)
     dominant = ("row_project", row_alg, row_t) if row_ms >= ax_ms else ("axis_fgi", ax_alg, ax_t)
     achieved = dominant[1] / dominant[2] / 1e9
+    traffic = recorded_traffic("k_row" if dominant[0] == "row_project" else "k_axis")
     roofline = {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": None,
+                "traffic": traffic,
                 "alg_bytes_per_launch": dominant[1], "launch_us": dominant[2] * 1e6,
                 "passes_us": {"row_project": row_t * 1e6, "axis_fgi": ax_t * 1e6},
                 "step_alg_bytes": row_alg + ax_alg,
