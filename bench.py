@@ -127,6 +127,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_throughput(points_per_rank: int, steps: int, seconds_local: float, device=None):
+    """Whole-job grid-point iterations/s over replicas: every rank iterates its
+    own field (no data-path collective); the job time is the max over ranks.
+    Returns (value, job_seconds)."""
+    import torch
+    import torch.distributed as dist
+
+    t = seconds_local
+    ws = 1
+    if dist.is_available() and dist.is_initialized():
+        ws = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return points_per_rank * steps * ws / t, t
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -312,12 +329,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms32, passes = time_steps(torch, h32, A32, args.steps, flush)
     barrier()
-    t32 = sum(ms32) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t32], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t32 = float(tt.item())
-    value = P * args.steps * ws / t32
+    value, t32 = job_throughput(P, args.steps, sum(ms32) / 1e3, device="cuda")
 
     # dominant kernel: the fused inverse-x / projection / forward-x pass
     hbm, peak_kind = load_peaks()
@@ -353,8 +365,8 @@ def run_ours(args, ws, rank, local):
         barrier()
         ms64, p64 = time_steps(torch, h64, A64, K64, flush)
         barrier()
-        t64 = sum(ms64) / 1e3
-        fp64 = {"value": P * K64 * ws / t64, "unit": UNIT, "steps": K64,
+        v64, t64 = job_throughput(P, K64, sum(ms64) / 1e3, device="cuda")
+        fp64 = {"value": v64, "unit": UNIT, "steps": K64,
                 "ms_per_step": 1e3 * t64 / K64,
                 "passes_us": {k: 1e3 * v[0] / max(v[1], 1) for k, v in p64.items() if v[1]}}
 
