@@ -288,7 +288,20 @@ static void complete_column(double* U, int n, int col, const int* have) {
  * the SVD; the flip form is the opposite-class minimiser of Lemma 7.1.
  * sigma (nullable) receives the singular values in descending order.
  * Returns the number of Jacobi sweeps. */
+static int polar_in_class(const double* M, double* B, double* sigma, int n, int cls);
+
 int orc_polar(const double* M, double* B, double* sigma, int n) {
+  return polar_in_class(M, B, sigma, n, 0);
+}
+
+/* Closest matrix of a prescribed class (cls = +1: SO(n), -1: SO^-(n)),
+ * Lemma 7.1: U V^t when the class is that of det M, otherwise U D_n V^t with
+ * D_n flipping the column of the smallest singular value. */
+int orc_polar_class(const double* M, double* B, int n, int cls) {
+  return polar_in_class(M, B, NULL, n, cls >= 0 ? 1 : -1);
+}
+
+static int polar_in_class(const double* M, double* B, double* sigma, int n, int cls) {
   if (n < 1 || n > ORC_MAXN) return -1;
   double a[ORC_MAXN * ORC_MAXN], v[ORC_MAXN * ORC_MAXN];
   memcpy(a, M, sizeof(double) * (size_t)(n * n));
@@ -336,17 +349,18 @@ int orc_polar(const double* M, double* B, double* sigma, int n) {
     if (sg[j] < sg[jmin]) jmin = j;
   int any = 0;
   for (int j = 0; j < n; ++j) any |= have[j];
-  if (!any) { /* A~ = 0: the identity. */
+  if (!any) { /* A~ = 0: the identity (diag(1, .., 1, -1) for the negative class). */
     for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) B[i * n + j] = (i == j) ? 1.0 : 0.0;
+      for (int j = 0; j < n; ++j) B[i * n + j] = (i == j) ? ((cls < 0 && i == n - 1) ? -1.0 : 1.0) : 0.0;
     if (sigma)
       for (int j = 0; j < n; ++j) sigma[j] = 0.0;
     return sweeps;
   }
   for (int j = 0; j < n; ++j)
     if (!have[j]) { complete_column(U, n, j, have); have[j] = 1; }
-  /* Enforce sign det(U V^t) = sign det M by the smallest-singular-value column. */
-  double want = (orc_det(M, n) >= 0.0) ? 1.0 : -1.0;
+  /* Enforce sign det(U V^t) = sign det M (or the prescribed class) by the
+   * smallest-singular-value column. */
+  double want = cls != 0 ? (double)cls : ((orc_det(M, n) >= 0.0) ? 1.0 : -1.0);
   double du = orc_det(U, n), dv = orc_det(v, n);
   if ((du * dv >= 0.0 ? 1.0 : -1.0) != want)
     for (int i = 0; i < n; ++i) U[i * n + jmin] = -U[i * n + jmin];
@@ -628,3 +642,88 @@ int orc_run(double* A, int ndim, const int64_t* dims, int n, double tau, int max
   if (stationary) *stationary = stat;
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Volume-preserving step (Sec. 7): T+ / T- are the closest matrices of     */
+/* SO(n) / SO^-(n) (Lemma 7.1), dE(x) = <T+(A~) - T-(A~), A~>_F, and the      */
+/* n_plus points of largest dE (the set {dE >= lambda} of Lemma 7.2 on a      */
+/* uniform grid, Algorithm 3 with equal weights) take T+, the others T-.      */
+/* Equal dE values are ordered by grid index (lower index first).             */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { double de; int64_t idx; } de_item;
+static int de_cmp(const void* a, const void* b) {
+  const de_item* x = (const de_item*)a;
+  const de_item* y = (const de_item*)b;
+  if (x->de > y->de) return -1;
+  if (x->de < y->de) return 1;
+  return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+double orc_delta_energy(const double* M, int n) {
+  double Tp[ORC_MAXN * ORC_MAXN], Tm[ORC_MAXN * ORC_MAXN];
+  orc_polar_class(M, Tp, n, 1);
+  orc_polar_class(M, Tm, n, -1);
+  double s = 0;
+  for (int c = 0; c < n * n; ++c) s += (Tp[c] - Tm[c]) * M[c];
+  return s;
+}
+
+/* Number of points whose (orthogonal) matrix has det > 0. */
+int64_t orc_count_positive(const double* A, int64_t P, int n) {
+  int64_t cnt = 0;
+  for (int64_t x = 0; x < P; ++x) {
+    double M[ORC_MAXN * ORC_MAXN];
+    for (int c = 0; c < n * n; ++c) M[c] = A[c * P + x];
+    if (orc_det(M, n) > 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+/* One volume-preserving step in place; n_plus < 0 keeps the count of A. */
+int orc_step_volume(double* A, int ndim, const int64_t* dims, int n, double tau, int64_t n_plus,
+                    orc_stats* st, double* dE_out) {
+  int64_t P = 1;
+  for (int a = 0; a < ndim; ++a) P *= dims[a];
+  int C = n * n;
+  if (n_plus < 0) n_plus = orc_count_positive(A, P, n);
+  if (n_plus > P) return 1;
+  double* At = (double*)malloc(sizeof(double) * (size_t)(P * C));
+  double mi = 0;
+  int rc = orc_diffuse(A, At, ndim, dims, C, tau, &mi);
+  if (rc) { free(At); return rc; }
+  double energy = orc_energy_from(A, At, ndim, dims, n, tau);
+  de_item* items = (de_item*)malloc(sizeof(de_item) * (size_t)P);
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < P; ++x) {
+    double M[ORC_MAXN * ORC_MAXN];
+    for (int c = 0; c < C; ++c) M[c] = At[c * P + x];
+    items[x].de = orc_delta_energy(M, n);
+    items[x].idx = x;
+  }
+  if (dE_out)
+    for (int64_t x = 0; x < P; ++x) dE_out[x] = items[x].de;
+  qsort(items, (size_t)P, sizeof(de_item), de_cmp);
+  double md = 0;
+  int64_t flips = 0;
+  for (int64_t r = 0; r < P; ++r) {
+    int64_t x = items[r].idx;
+    double M[ORC_MAXN * ORC_MAXN], Bx[ORC_MAXN * ORC_MAXN], Mo[ORC_MAXN * ORC_MAXN];
+    for (int c = 0; c < C; ++c) {
+      M[c] = At[c * P + x];
+      Mo[c] = A[c * P + x];
+    }
+    orc_polar_class(M, Bx, n, r < n_plus ? 1 : -1);
+    for (int c = 0; c < C; ++c) {
+      double d = fabs(Bx[c] - Mo[c]);
+      if (d > md) md = d;
+      A[c * P + x] = Bx[c];
+    }
+    if ((orc_det(Mo, n) > 0.0) != (r < n_plus)) ++flips;
+  }
+  free(items);
+  free(At);
+  if (st) { st->energy = energy; st->max_delta = md; st->det_flips = flips; st->max_imag = mi; }
+  return 0;
+}
+

@@ -67,6 +67,14 @@ def _load():
                             C.POINTER(C.c_int), C.POINTER(C.c_int), dp, dp, i64p]
     lib.orc_step_points.argtypes = [dp, C.c_int, i64p, C.c_int, C.c_double, C.c_int, i64p,
                                     C.c_int64, dp, dp]
+    lib.orc_polar_class.argtypes = [dp, dp, C.c_int, C.c_int]
+    lib.orc_polar_class.restype = C.c_int
+    lib.orc_delta_energy.argtypes = [dp, C.c_int]
+    lib.orc_delta_energy.restype = C.c_double
+    lib.orc_count_positive.argtypes = [dp, C.c_int64, C.c_int]
+    lib.orc_count_positive.restype = C.c_int64
+    lib.orc_step_volume.argtypes = [dp, C.c_int, i64p, C.c_int, C.c_double, C.c_int64, C.c_void_p, dp]
+    lib.orc_step_volume.restype = C.c_int
     lib.orc_step_points_f32.argtypes = [C.POINTER(C.c_float), C.c_int, i64p, C.c_int, C.c_double,
                                         C.c_int, i64p, C.c_int64, dp, dp]
     for f in ("orc_fft", "orc_dft_direct", "orc_fftn", "orc_heat_multiplier", "orc_diffuse",
@@ -216,6 +224,35 @@ def step_points(A: np.ndarray, n: int, tau: float, pts, project_input: bool = Fa
                                      1 if project_input else 0, pp, npts, _dp(At), _dp(B))
     _check(rc, "step_points")
     return At, B
+
+
+def polar_class(M: np.ndarray, cls: int) -> np.ndarray:
+    """Closest matrix of SO(n) (cls = +1) or SO^-(n) (cls = -1), Lemma 7.1."""
+    M = _f64(M)
+    B = np.empty_like(M)
+    _load().orc_polar_class(_dp(M), _dp(B), M.shape[0], int(cls))
+    return B
+
+
+def delta_energy(M: np.ndarray) -> float:
+    """<T+(M) - T-(M), M>_F (Sec. 7)."""
+    M = _f64(M)
+    return _load().orc_delta_energy(_dp(M), M.shape[0])
+
+
+def count_positive(A: np.ndarray, n: int) -> int:
+    A = _f64(A)
+    return int(_load().orc_count_positive(_dp(A), int(np.prod(A.shape[1:])), n))
+
+
+def step_volume(A: np.ndarray, n: int, tau: float, n_plus: int = -1):
+    """One volume-preserving step (Sec. 7); returns (A_next, stats, dE)."""
+    A = _f64(A).copy()
+    st = OracleStats()
+    dE = np.empty(A.shape[1:])
+    _check(_load().orc_step_volume(_dp(A), A.ndim - 1, _dims(A.shape[1:]), n, float(tau),
+                                   int(n_plus), C.byref(st), _dp(dE)), "step_volume")
+    return A, {"energy": st.energy, "max_delta": st.max_delta, "det_flips": st.det_flips}, dE
 
 
 def run(A: np.ndarray, n: int, tau: float, max_steps: int, tol: float):

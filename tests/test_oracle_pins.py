@@ -433,3 +433,70 @@ def test_step_at_points_matches_full_step(dims, n):
         At_p, B_p = O.step_points(raw, n, tau, pts, project_input=True)
         assert np.abs(At_p - At[idx].T).max() < 1e-14
         assert np.abs(B_p - B[idx].T).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Volume-preserving variant (Sec. 7: Lemma 7.1, Lemma 7.2, Prop. 7.3, Alg. 3)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_class_projections_and_delta_energy_closed_form(n):
+    """T+ in SO(n), T- in SO^-(n), T^{sign det M} = polar(M), and
+    <T+ - T-, M> = 2 sign(det M) sigma_min (they differ in one rank-one term)."""
+    g = I.rng(300 + n)
+    for _ in range(100):
+        M = g.standard_normal((n, n))
+        Tp, Tm = O.polar_class(M, 1), O.polar_class(M, -1)
+        assert np.linalg.det(Tp) == pytest.approx(1.0) and np.linalg.det(Tm) == pytest.approx(-1.0)
+        assert np.allclose(Tp.T @ Tp, np.eye(n)) and np.allclose(Tm.T @ Tm, np.eye(n))
+        own = Tp if np.linalg.det(M) >= 0 else Tm
+        assert np.allclose(own, O.polar(M), atol=1e-13)
+        s = np.linalg.svd(M, compute_uv=False)
+        assert O.delta_energy(M) == pytest.approx(2 * np.sign(np.linalg.det(M)) * s[-1], rel=1e-10,
+                                                  abs=1e-13)
+
+
+def test_volume_step_is_optimal_by_brute_force():
+    """Lemma 7.2: among all assignments with exactly n_plus points in SO(n),
+    the chosen one maximises sum_x <B(x), A~(x)> (minimises the linearisation)."""
+    dims, n, tau = (2, 4), 2, 0.01
+    A0 = O.project(I.gaussian(dims, n, 91), n)
+    At = O.diffuse(A0, tau)
+    Mx = At.reshape(4, -1).T.reshape(-1, 2, 2)
+    P = Mx.shape[0]
+    for n_plus in range(P + 1):
+        B, _, _ = O.step_volume(A0, n, tau, n_plus)
+        Bx = B.reshape(4, -1).T.reshape(-1, 2, 2)
+        got = sum(np.sum(Bx[i] * Mx[i]) for i in range(P))
+        assert sum(np.linalg.det(b) > 0 for b in Bx) == n_plus
+        best = -np.inf
+        for S in itertools.combinations(range(P), n_plus):
+            val = sum(np.sum(O.polar_class(Mx[i], 1 if i in S else -1) * Mx[i]) for i in range(P))
+            best = max(best, val)
+        assert got == pytest.approx(best, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_volume_preserving_iteration_keeps_volume_and_energy_decreases(n):
+    """Prop. 7.3: E^tau non-increasing; the SO(n) count stays n_plus."""
+    dims = (24, 24)
+    tau = 4.0 / 24 ** 2
+    A = O.project(I.gaussian(dims, n, 400 + n), n)
+    n_plus = O.count_positive(A, n)
+    E = O.energy(A, n, tau)
+    for _ in range(8):
+        A, st, _ = O.step_volume(A, n, tau)
+        assert st["energy"] == pytest.approx(E, rel=1e-12)
+        assert O.count_positive(A, n) == n_plus
+        E_new = O.energy(A, n, tau)
+        assert E_new <= E * (1 + 1e-13) + 1e-12
+        E = E_new
+
+
+def test_volume_step_reduces_to_plain_step_when_counts_agree():
+    dims, n = (16, 16), 3
+    tau = 3.0 / 256
+    A0 = O.project(I.gaussian(dims, n, 77), n)
+    B, _ = O.step(A0, n, tau)
+    Bv, _, _ = O.step_volume(A0, n, tau, O.count_positive(B, n))
+    assert np.abs(B - Bv).max() < 1e-14
