@@ -200,6 +200,32 @@ MBO_API mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, dou
                                        void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Volume-preserving MBO (Sec. 7).  The diffusion step is unchanged; the     */
+/* projection is replaced by the assignment of Lemma 7.2: with T+ / T- the   */
+/* closest matrices of SO(n) / SO^-(n) to A~(x) (Lemma 7.1) and              */
+/* dE(x) = <T+ - T-, A~(x)>_F = 2 sign(det A~) sigma_min(A~), the n_plus      */
+/* points of largest dE take T+ and all others T- (Algorithm 3 on a uniform   */
+/* grid); equal dE values are ordered by grid index, lower index first.      */
+/* ------------------------------------------------------------------------- */
+
+/* One volume-preserving step in place.  n_plus: the number of points that
+ * lie in SO(n) after the step (0 <= n_plus <= P); < 0 keeps the number of
+ * points of A with det > 0.  stats as in mbo_step (energy of the input).
+ * Allocates the step's buffers (a field copy and 8 bytes per point) on first
+ * use. */
+MBO_API mbo_status mbo_step_volume(mbo_handle h, void* A, int64_t n_plus, mbo_stats* stats,
+                                   void* stream);
+
+/* Iterate the volume-preserving step until stationary (as
+ * mbo_run_until_stationary) with the SO(n) point count fixed at n_plus (< 0:
+ * that of the initial field).  A: device field.  energies (nullable,
+ * max_steps + 1 values; the last 1024 steps when the run is longer).
+ * Synchronises. */
+MBO_API mbo_status mbo_run_volume(mbo_handle h, void* A, int64_t n_plus, int max_steps, double tol,
+                                  int* steps_taken, int* stationary, double* energies,
+                                  void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Batches of independent fields.  Fields may differ in ndim, dims, n and tau */
 /* (one dtype per batch).  One step of the batch runs every field's step     */
 /* (Algorithm 1) from a single CUDA graph launch whose per-field branches are */

@@ -127,6 +127,10 @@ struct mbo_ctx {
   Hist hist{};
   void* hist_mem = nullptr;
   void* field = nullptr;  // staging field for host-pointer runs
+  // volume-preserving step buffers (allocated on first use)
+  void* vp_at = nullptr;                 // the diffused field
+  unsigned long long* vp_keys = nullptr; // one selection key per point
+  SelectState* vp_ss = nullptr;
   // host mirrors
   RunState* h_st = nullptr;  // pinned
   void* h_hist = nullptr;    // pinned ring copy
@@ -401,6 +405,9 @@ mbo_status mbo_destroy(mbo_handle h) {
   cudaFree(h->st);
   cudaFree(h->hist_mem);
   cudaFree(h->field);
+  cudaFree(h->vp_at);
+  cudaFree(h->vp_keys);
+  cudaFree(h->vp_ss);
   cudaFreeHost(h->h_st);
   cudaFreeHost(h->h_hist);
   delete h;
@@ -773,6 +780,121 @@ mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npa
     if (ms) ms[i] = h->prof_ms[i];
     if (launches) launches[i] = h->prof_n[i];
   }
+  return MBO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Volume-preserving MBO (Sec. 7)
+// ---------------------------------------------------------------------------
+
+static mbo_status vp_buffers(mbo_handle h) {
+  if (h->vp_at) return MBO_OK;
+  const size_t fbytes = (size_t)h->g.C * (size_t)h->g.P * h->elem;
+  CK(cudaMalloc(&h->vp_at, fbytes));
+  CK(cudaMalloc((void**)&h->vp_keys, (size_t)h->g.P * sizeof(unsigned long long)));
+  CK(cudaMalloc((void**)&h->vp_ss, sizeof(SelectState)));
+  h->bytes_total += fbytes + (size_t)h->g.P * 8 + sizeof(SelectState);
+  return MBO_OK;
+}
+
+static cudaError_t vp_launch(mbo_handle h, int which, const void* At, void* A, const StatsPtrs& sp,
+                             cudaStream_t s) {
+  long long blocks = (h->g.P + 255) / 256;
+  const long long cap = std::min<long long>((long long)h->ngroups * kReduceGroup, 152 * 16);
+  if (blocks > cap) blocks = cap;
+  if (h->dtype == MBO_F32)
+    return launch_volume<float>(which, h->g, static_cast<const float*>(At), static_cast<float*>(A),
+                                h->vp_keys, h->vp_ss, sp, h->cfg.fallback_sigma, (int)blocks, s);
+  return launch_volume<double>(which, h->g, static_cast<const double*>(At), static_cast<double*>(A),
+                               h->vp_keys, h->vp_ss, sp, 0.0, (int)blocks, s);
+}
+
+// One volume-preserving step: diffuse (energy of A recorded), dE keys,
+// selection of n_plus (< 0: the count of det > 0 points of A), assignment.
+static mbo_status vp_step(mbo_handle h, void* A, long long n_plus, bool respect_stop, double tol,
+                          cudaStream_t s) {
+  const StatsPtrs sp = stats_ptrs(h, true, respect_stop, tol);
+  StatsPtrs none = sp;
+  none.do_stats = 0;
+  CK(row_pass(h, ROW_FWD, A, nullptr, sp, s));
+  CK(middle_passes(h, AXIS_FGI, sp, s));
+  CK(row_pass(h, ROW_INV_OUT, nullptr, h->vp_at, none, s));
+  CK(vp_launch(h, 0, h->vp_at, A, none, s));
+  if (n_plus < 0) {
+    CK(cudaMemsetAsync(&h->vp_ss->n_plus, 0, sizeof(unsigned long long), s));
+    CK(vp_launch(h, 1, h->vp_at, A, none, s));
+  }
+  CK(launch_select_init(h->vp_ss, n_plus, s));
+  long long blocks = std::min<long long>((h->g.P + 255) / 256, 152 * 16);
+  CK(launch_select(h->vp_keys, h->g.P, h->vp_ss, (int)blocks, s));
+  CK(vp_launch(h, 2, h->vp_at, A, sp, s));
+  h->w_valid_for = nullptr;
+  return MBO_OK;
+}
+
+mbo_status mbo_step_volume(mbo_handle h, void* A, int64_t n_plus, mbo_stats* stats, void* stream) {
+  if (!h) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
+  if (n_plus > h->g.P) return fail(h, MBO_ERR_INVALID_ARG, "n_plus exceeds the number of points");
+  DeviceGuard dg(h->dev);
+  if ((rc = vp_buffers(h)) != MBO_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = vp_step(h, A, n_plus, false, -1.0, s)) != MBO_OK) return rc;
+  if (stats) {
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+    const long long slot = (h->h_st->step - 1) & (kRing - 1);
+    if ((rc = read_record(h, slot, stats)) != MBO_OK) return rc;
+    if (stats->nonfinite) return fail(h, MBO_ERR_NUMERIC, "%lld non-finite points", (long long)stats->nonfinite);
+  }
+  return MBO_OK;
+}
+
+mbo_status mbo_run_volume(mbo_handle h, void* A, int64_t n_plus, int max_steps, double tol,
+                          int* steps_taken, int* stationary, double* energies, void* stream) {
+  if (!h || max_steps < 0) return MBO_ERR_INVALID_ARG;
+  mbo_status rc;
+  if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
+  if (n_plus > h->g.P) return fail(h, MBO_ERR_INVALID_ARG, "n_plus exceeds the number of points");
+  DeviceGuard dg(h->dev);
+  if ((rc = vp_buffers(h)) != MBO_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(h->st, 0, sizeof(RunState), s));
+  if (n_plus < 0) {  // fix the volume of the initial field once
+    const StatsPtrs none = stats_ptrs(h, false, false, -1.0);
+    CK(cudaMemsetAsync(&h->vp_ss->n_plus, 0, sizeof(unsigned long long), s));
+    CK(vp_launch(h, 1, nullptr, A, none, s));
+    unsigned long long cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, &h->vp_ss->n_plus, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    n_plus = (long long)cnt;
+  }
+  const int K = h->cfg.check_interval;
+  int done = 0;
+  bool stopped = false;
+  while (done < max_steps && !stopped) {
+    const int chunk = std::min(K, max_steps - done);
+    for (int i = 0; i < chunk; ++i)
+      if ((rc = vp_step(h, A, n_plus, true, tol, s)) != MBO_OK) return rc;
+    done += chunk;
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    stopped = h->h_st->stop != 0;
+  }
+  const long long steps = h->h_st->step;
+  CK(row_pass(h, ROW_FWD, A, nullptr, stats_ptrs(h, true, false, -1.0), s));
+  CK(middle_passes(h, AXIS_ENERGY, stats_ptrs(h, true, false, -1.0), s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(h->h_hist, h->hist_mem, (size_t)kRing * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+  const double* hh = static_cast<const double*>(h->h_hist);
+  if (energies) {
+    const long long first = std::max(0LL, steps + 1 - kRing);
+    for (long long i = first; i <= steps; ++i) energies[i] = hh[i & (kRing - 1)];
+  }
+  h->w_valid_for = (h->g.ndim == 2) ? A : nullptr;
+  if (steps_taken) *steps_taken = (int)steps;
+  if (stationary) *stationary = stopped ? 1 : 0;
   return MBO_OK;
 }
 

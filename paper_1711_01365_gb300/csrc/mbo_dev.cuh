@@ -338,16 +338,23 @@ template <typename R> __device__ __forceinline__ void any_orthogonal(const R* u,
   w[0] = x[0] * inv; w[1] = x[1] * inv; w[2] = x[2] * inv;
 }
 
-// n = 3: one-sided (Hestenes) Jacobi on the columns of m, then
-// U = [u_big, u_mid, +-u_big x u_mid] (orthonormal by construction, with the
-// smallest-singular-value column oriented so that det(U V^t) = sign det m),
-// V re-orthonormalised, b = U V^t.
-template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& smin) {
-  const R det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
-                m[2] * (m[3] * m[7] - m[4] * m[6]);
-  const R sg = (det >= R(0)) ? R(1) : R(-1);
-  R a[3][3] = {{m[0], m[3], m[6]}, {m[1], m[4], m[7]}, {m[2], m[5], m[8]}};  // a[j] = column j
-  R v[3][3] = {{R(1), R(0), R(0)}, {R(0), R(1), R(0)}, {R(0), R(0), R(1)}};
+// n = 3: one-sided (Hestenes) Jacobi on the columns of m.  On return
+// a[j] = m v_j (mutually orthogonal columns), V = [v_0 v_1 v_2] in SO(3)
+// (re-orthonormalised), and U in SO(3) with columns u_big = a_big / |a_big|,
+// u_mid from Gram-Schmidt and u_small = +-u_big x u_mid (orientation chosen
+// so det U = +1); is = index of the smallest column, smin = |a_is|.  Then
+// m = U diag(s_j) V^t with s_is = u_is . a_is carrying the sign of det m.
+// Returns false (frame undefined) when m = 0 or is not finite.
+template <typename R>
+__device__ __forceinline__ bool jacobi3_frame(const R* m, R (&U)[3][3], R (&v)[3][3], R (&a)[3][3],
+                                              int& is, R& smin) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a[j][i] = m[i * 3 + j];
+      v[j][i] = (i == j) ? R(1) : R(0);
+    }
 #pragma unroll 1
   for (int sw = 0; sw < JacobiPrec<R>::sweeps; ++sw) {
     bool rot = false;
@@ -358,7 +365,8 @@ template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& s
   }
   const R n0 = dot3(a[0], a[0]), n1 = dot3(a[1], a[1]), n2 = dot3(a[2], a[2]);
   // order the columns: ib (largest), im, is (smallest)
-  int ib = 0, is = 0;
+  int ib = 0;
+  is = 0;
   if (n1 > n0) ib = 1;
   if (n2 > (ib == 0 ? n0 : n1)) ib = 2;
   if (n1 < n0) is = 1;
@@ -367,18 +375,13 @@ template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& s
   const int im = 3 - ib - is;
   const R nn[3] = {n0, n1, n2};
   smin = sqrt(nn[is]);
-  if (!(nn[ib] > R(0))) {  // m = 0 (or not finite): identity
-#pragma unroll
-    for (int i = 0; i < 9; ++i) b[i] = (i % 4 == 0) ? R(1) : R(0);
-    return (nn[ib] == R(0)) ? R(1) : sg;
-  }
-  R U[3][3];  // U[j] = column j
+  if (!(nn[ib] > R(0))) return false;
   {
     const R inv = rsqrt_(nn[ib]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) U[ib][i] = a[ib][i] * inv;
-    const R d = dot3(U[ib], a[im]);
-    R w[3] = {a[im][0] - d * U[ib][0], a[im][1] - d * U[ib][1], a[im][2] - d * U[ib][2]};
+    const R dd = dot3(U[ib], a[im]);
+    R w[3] = {a[im][0] - dd * U[ib][0], a[im][1] - dd * U[ib][1], a[im][2] - dd * U[ib][2]};
     const R ww = dot3(w, w);
     if (ww > R(0) && ww > nn[ib] * R(1e-30)) {
       const R iw = rsqrt_(ww);
@@ -390,24 +393,94 @@ template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& s
     const R perm = (im == (ib + 1) % 3) ? R(1) : R(-1);
     R c[3];
     cross3(U[ib], U[im], c);
-    const R f = perm * sg;
-    U[is][0] = f * c[0]; U[is][1] = f * c[1]; U[is][2] = f * c[2];
+    U[is][0] = perm * c[0]; U[is][1] = perm * c[1]; U[is][2] = perm * c[2];
   }
   // re-orthonormalise V (a product of rotations: keep det V = +1)
   {
     const R i0 = rsqrt_(dot3(v[0], v[0]));
     v[0][0] *= i0; v[0][1] *= i0; v[0][2] *= i0;
-    const R d = dot3(v[0], v[1]);
-    v[1][0] -= d * v[0][0]; v[1][1] -= d * v[0][1]; v[1][2] -= d * v[0][2];
+    const R dd = dot3(v[0], v[1]);
+    v[1][0] -= dd * v[0][0]; v[1][1] -= dd * v[0][1]; v[1][2] -= dd * v[0][2];
     const R i1 = rsqrt_(dot3(v[1], v[1]));
     v[1][0] *= i1; v[1][1] *= i1; v[1][2] *= i1;
     cross3(v[0], v[1], v[2]);
   }
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ void frame_product(const R (&U)[3][3], const R (&v)[3][3], R* b) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[i * 3 + k] = U[0][i] * v[0][k] + U[1][i] * v[1][k] + U[2][i] * v[2][k];
+}
+
+// n = 3 polar factor from the Jacobi frame: U V^t with the smallest column of
+// U oriented so that det(U V^t) = sign det m (Lemma 1.1; det m = 0 -> +1).
+template <typename R> __device__ __forceinline__ R polar3(const R* m, R* b, R& smin) {
+  const R det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                m[2] * (m[3] * m[7] - m[4] * m[6]);
+  const R sg = (det >= R(0)) ? R(1) : R(-1);
+  R U[3][3], v[3][3], a[3][3];
+  int is;
+  if (!jacobi3_frame(m, U, v, a, is, smin)) {  // m = 0 (or not finite): identity
+#pragma unroll
+    for (int i = 0; i < 9; ++i) b[i] = (i % 4 == 0) ? R(1) : R(0);
+    return (a[0][0] == R(0) && a[1][1] == R(0) && a[2][2] == R(0)) ? R(1) : sg;
+  }
+  U[is][0] *= sg; U[is][1] *= sg; U[is][2] *= sg;
+  frame_product(U, v, b);
   return sg;
+}
+
+// Closest matrices of SO(n) (tp) and SO^-(n) (tm) and dE = <tp - tm, m>_F
+// (Lemma 7.1, Sec. 7).  Returns the smallest singular value.
+template <int NM, typename R>
+__device__ __forceinline__ R class_pair(const R* m, R* tp, R* tm, R& dE) {
+  if constexpr (NM == 1) {
+    tp[0] = R(1);
+    tm[0] = R(-1);
+    dE = R(2) * m[0];
+    return fabs(m[0]);
+  } else if constexpr (NM == 2) {
+    const R p = m[0] + m[3], q = m[2] - m[1], r = m[0] - m[3], t = m[1] + m[2];
+    const R rho = sqrt(p * p + q * q), sig = sqrt(r * r + t * t);
+    if (rho > R(0)) {
+      const R i = R(1) / rho;
+      tp[0] = p * i; tp[1] = -q * i; tp[2] = q * i; tp[3] = p * i;
+    } else {
+      tp[0] = R(1); tp[1] = R(0); tp[2] = R(0); tp[3] = R(1);
+    }
+    if (sig > R(0)) {
+      const R i = R(1) / sig;
+      tm[0] = r * i; tm[1] = t * i; tm[2] = t * i; tm[3] = -r * i;
+    } else {
+      tm[0] = R(1); tm[1] = R(0); tm[2] = R(0); tm[3] = R(-1);
+    }
+    dE = rho - sig;  // <rotation, m> = |(p, q)|, <reflection, m> = |(r, t)|
+    return R(0.5) * fabs(rho - sig);
+  } else {
+    R U[3][3], v[3][3], a[3][3], smin;
+    int is;
+    if (!jacobi3_frame(m, U, v, a, is, smin)) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        tp[i] = (i % 4 == 0) ? R(1) : R(0);
+        tm[i] = (i % 4 == 0) ? (i == 8 ? R(-1) : R(1)) : R(0);
+      }
+      dE = R(0);
+      return smin;
+    }
+    frame_product(U, v, tp);  // U, V in SO(3): the closest rotation
+    const R s = dot3(U[is], a[is]);  // signed smallest singular value
+    dE = R(2) * s;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tm[i * 3 + k] = tp[i * 3 + k] - R(2) * U[is][i] * v[is][k];
+    return smin;
+  }
 }
 
 // Reciprocal of a nonzero value: correctly rounded in FP32; in FP64 an FP32

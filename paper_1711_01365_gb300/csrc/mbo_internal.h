@@ -103,6 +103,22 @@ struct StatsPtrs {
   double tol;          // stationarity tolerance (< 0: never stop)
 };
 
+// Radix selection of the n_plus smallest (key, index) pairs (volume-preserving
+// step).  After the passes, (hi, lo) is the n_plus-th smallest pair; a point is
+// selected iff (key, index) <= (hi, lo) and n_plus > 0.
+struct SelectState {
+  unsigned long long hi;     // key part of the prefix / result
+  unsigned int lo;           // index part
+  unsigned int pad_;
+  unsigned long long k;      // remaining rank (1-based) inside the current prefix
+  unsigned long long n_plus; // points to select
+  unsigned int hist[256];
+};
+
+cudaError_t launch_select(unsigned long long* keys, long long P, SelectState* ss, int blocks,
+                          cudaStream_t s);
+cudaError_t launch_select_init(SelectState* ss, long long n, cudaStream_t s);
+
 // Launchers (defined per element type in k_f32.cu / k_f64.cu).
 template <typename R>
 cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R* A_in, R* A_out,
@@ -123,6 +139,10 @@ int plan_twiddles(const Plan& p);
 int pick_tx(int nx, int cap);
 
 template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx);
+template <typename R>
+cudaError_t launch_volume(int which, const Geom& g, const R* At, R* A, unsigned long long* keys,
+                          SelectState* ss, const StatsPtrs& sp, double fb, int blocks,
+                          cudaStream_t s);
 
 // Shared memory bytes of the row kernel for a geometry.
 size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback);

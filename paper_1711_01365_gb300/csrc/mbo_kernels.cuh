@@ -92,6 +92,49 @@ __device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, lon
   for (int q = 0; q < Q; ++q) s[lay.addr(q, x)] = V{b[2 * q], (2 * q + 1 < C) ? b[2 * q + 1] : R(0)};
 }
 
+// Reduce a block's point statistics and, in the last block of the grid,
+// record the step (energy slot filled earlier by the transform pass; max
+// delta, flips, re-projections, non-finite count), decide stationarity
+// (tol >= 0), reset the accumulators and advance the step counter.
+template <typename R>
+__device__ __forceinline__ void finalize_step_stats(const StatsPtrs& sp, const PointStats<R>& ps,
+                                                    double* redd, int* redi, int* s_flag) {
+  const int tid = threadIdx.x;
+  const double dsum = block_sum((double)ps.defect, redd);
+  const double mx = block_max((double)ps.maxd, redd);
+  const int fl = block_sum(ps.flips, redi);
+  const int nfin = block_sum(ps.nonfinite, redi);
+  const int nfb = block_sum(ps.fallback, redi);
+  if (tid == 0) {
+    atomicMax(&sp.st->maxdelta_bits, (unsigned long long)__double_as_longlong(mx));
+    if (fl) atomicAdd(&sp.st->flips, (unsigned long long)fl);
+    if (nfin) atomicAdd(&sp.st->nonfinite, (unsigned long long)nfin);
+    if (nfb) atomicAdd(&sp.st->fallback, (unsigned long long)nfb);
+  }
+  double all;
+  if (grid_sum(dsum, sp.rb, redd, s_flag, &all)) {
+    if (tid == 0) {
+      RunState* st = sp.st;
+      st->defect = all;
+      const long long slot = st->step & (kRing - 1);
+      const double md = __longlong_as_double((long long)atomicAdd(&st->maxdelta_bits, 0ull));
+      const unsigned long long f = atomicAdd(&st->flips, 0ull);
+      const unsigned long long nb = atomicAdd(&st->fallback, 0ull);
+      const unsigned long long nn = atomicAdd(&st->nonfinite, 0ull);
+      sp.hist.maxdelta[slot] = md;
+      sp.hist.flips[slot] = (long long)f;
+      sp.hist.fallback[slot] = (long long)nb;
+      sp.hist.nonfinite[slot] = (long long)nn;
+      if (sp.tol >= 0.0 && f == 0 && md <= sp.tol) st->stop = 1;
+      st->maxdelta_bits = 0;
+      st->flips = 0;
+      st->fallback = 0;
+      st->nonfinite = 0;
+      st->step += 1;
+    }
+  }
+}
+
 template <typename R, int NM, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, sizeof(R) == 4 ? 2 : 1)
 k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W, StatsPtrs sp,
@@ -219,39 +262,7 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
     for (int x = tid; x < nx; x += T) W[q * P + off + x] = s[lay.addr(q, x)];
 
   if (!sp.do_stats) return;
-  const double dsum = block_sum((double)ps.defect, redd);
-  const double mx = block_max((double)ps.maxd, redd);
-  const int fl = block_sum(ps.flips, redi);
-  const int nfin = block_sum(ps.nonfinite, redi);
-  const int nfb = block_sum(ps.fallback, redi);
-  if (tid == 0) {
-    atomicMax(&sp.st->maxdelta_bits, (unsigned long long)__double_as_longlong(mx));
-    if (fl) atomicAdd(&sp.st->flips, (unsigned long long)fl);
-    if (nfin) atomicAdd(&sp.st->nonfinite, (unsigned long long)nfin);
-    if (nfb) atomicAdd(&sp.st->fallback, (unsigned long long)nfb);
-  }
-  double all;
-  if (grid_sum(dsum, sp.rb, redd, &s_flag, &all)) {
-    if (tid == 0) {
-      RunState* st = sp.st;
-      st->defect = all;
-      const long long slot = st->step & (kRing - 1);
-      const double md = __longlong_as_double((long long)atomicAdd(&st->maxdelta_bits, 0ull));
-      const unsigned long long f = atomicAdd(&st->flips, 0ull);
-      const unsigned long long nb = atomicAdd(&st->fallback, 0ull);
-      const unsigned long long nn = atomicAdd(&st->nonfinite, 0ull);
-      sp.hist.maxdelta[slot] = md;
-      sp.hist.flips[slot] = (long long)f;
-      sp.hist.fallback[slot] = (long long)nb;
-      sp.hist.nonfinite[slot] = (long long)nn;
-      if (sp.tol >= 0.0 && f == 0 && md <= sp.tol) st->stop = 1;
-      st->maxdelta_bits = 0;
-      st->flips = 0;
-      st->fallback = 0;
-      st->nonfinite = 0;
-      st->step += 1;
-    }
-  }
+  finalize_step_stats(sp, ps, redd, redi, &s_flag);
 }
 
 // Strided-axis pass (y in 2-D; y and z in 3-D).  One block owns a tile of tx
@@ -358,6 +369,153 @@ k_project(long long P, const R* At, R* B, int8_t* ds, R fb_sigma) {
     for (int c = 0; c < C; ++c) B[c * P + x] = b[c];
     if (ds) ds[x] = (sg > R(0)) ? 1 : -1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Volume-preserving step (Sec. 7)
+// ---------------------------------------------------------------------------
+
+// Order-preserving map of a double to an unsigned 64-bit key, complemented so
+// that ascending keys are descending values.
+__device__ __forceinline__ unsigned long long desc_key(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned long long asc = (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+  return ~asc;
+}
+
+// dE and both class candidates of a point in R, re-done in FP64 where the FP32
+// smallest singular value is below fb.
+template <int NM, typename R>
+__device__ __forceinline__ R class_pair_checked(const R* m, R* tp, R* tm, R& dE, R fb, int& fbk) {
+  const R smin = class_pair<NM>(m, tp, tm, dE);
+  if (sizeof(R) == 4 && NM >= 2 && smin < fb) {
+    constexpr int C = NM * NM;
+    double md[C], pd[C], qd[C], ed;
+#pragma unroll
+    for (int c = 0; c < C; ++c) md[c] = (double)m[c];
+    class_pair<NM>(md, pd, qd, ed);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      tp[c] = (R)pd[c];
+      tm[c] = (R)qd[c];
+    }
+    dE = (R)ed;
+    fbk = 1;
+  }
+  return smin;
+}
+
+// keys[x] = desc_key(dE(x)) for the diffused field At.
+template <typename R, int NM>
+__global__ void __launch_bounds__(256)
+k_vp_delta(long long P, const R* __restrict__ At, unsigned long long* keys, R fb) {
+  constexpr int C = NM * NM;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < P;
+       x += (long long)gridDim.x * blockDim.x) {
+    R m[C], tp[C], tm[C], dE;
+    int fbk = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) m[c] = At[c * P + x];
+    class_pair_checked<NM>(m, tp, tm, dE, fb, fbk);
+    keys[x] = desc_key((double)dE);
+  }
+}
+
+// Points with det A(x) > 0 are counted into *count.
+template <typename R, int NM>
+__global__ void __launch_bounds__(256)
+k_count_positive(long long P, const R* __restrict__ A, unsigned long long* count) {
+  constexpr int C = NM * NM;
+  __shared__ int redi[32];
+  int cnt = 0;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < P;
+       x += (long long)gridDim.x * blockDim.x) {
+    R m[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) m[c] = A[c * P + x];
+    R d;
+    if constexpr (NM == 1) d = m[0];
+    else if constexpr (NM == 2) d = m[0] * m[3] - m[1] * m[2];
+    else
+      d = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+          m[2] * (m[3] * m[7] - m[4] * m[6]);
+    cnt += (d > R(0)) ? 1 : 0;
+  }
+  cnt = block_sum(cnt, redi);
+  if (threadIdx.x == 0 && cnt) atomicAdd(count, (unsigned long long)cnt);
+}
+
+// Assign T+ to the n_plus points of smallest (key, index) and T- to the rest,
+// write the field, and record the step like the projection pass.
+template <typename R, int NM>
+__global__ void __launch_bounds__(256)
+k_vp_assign(long long P, const R* __restrict__ At, R* A, const unsigned long long* __restrict__ keys,
+            const SelectState* __restrict__ ss, StatsPtrs sp, R fb) {
+  constexpr int C = NM * NM;
+  __shared__ double redd[32];
+  __shared__ int redi[32];
+  __shared__ int s_flag;
+  if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
+  const unsigned long long n_plus = ss->n_plus;
+  const unsigned long long kh = ss->hi;
+  const unsigned int kl = ss->lo;
+  PointStats<R> ps;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < P;
+       x += (long long)gridDim.x * blockDim.x) {
+    R m[C], tp[C], tm[C], old[C], dE;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      m[c] = At[c * P + x];
+      old[c] = A[c * P + x];
+    }
+    int fbk = 0;
+    class_pair_checked<NM>(m, tp, tm, dE, fb, fbk);
+    ps.fallback += fbk;
+    const unsigned long long k = keys[x];
+    const bool sel = n_plus > 0 && (k < kh || (k == kh && (unsigned int)x <= kl));
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+    ps.nonfinite += fin ? 0 : 1;
+    R d = R(0), nb = R(0);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R b = sel ? tp[c] : tm[c];
+      d = fmax(d, fabs(b - old[c]));
+      nb += b * b;
+      A[c * P + x] = b;
+    }
+    ps.maxd = fmax(ps.maxd, d);
+    ps.defect += R(NM) - nb;
+    R od;
+    if constexpr (NM == 1) od = old[0];
+    else if constexpr (NM == 2) od = old[0] * old[3] - old[1] * old[2];
+    else
+      od = old[0] * (old[4] * old[8] - old[5] * old[7]) - old[1] * (old[3] * old[8] - old[5] * old[6]) +
+           old[2] * (old[3] * old[7] - old[4] * old[6]);
+    ps.flips += ((od > R(0)) != sel) ? 1 : 0;
+  }
+  if (!sp.do_stats) return;
+  finalize_step_stats(sp, ps, redd, redi, &s_flag);
+}
+
+template <typename R>
+cudaError_t launch_volume(int which, const Geom& g, const R* At, R* A, unsigned long long* keys,
+                          SelectState* ss, const StatsPtrs& sp, double fb, int blocks,
+                          cudaStream_t s) {
+  const R f = (R)fb;
+#define MBO_VP_CASE(NM)                                                                         \
+  if (g.n == NM) {                                                                              \
+    if (which == 0) k_vp_delta<R, NM><<<blocks, 256, 0, s>>>(g.P, At, keys, f);                 \
+    else if (which == 1) k_count_positive<R, NM><<<blocks, 256, 0, s>>>(g.P, A, &ss->n_plus);   \
+    else k_vp_assign<R, NM><<<blocks, 256, 0, s>>>(g.P, At, A, keys, ss, sp, f);                \
+    return cudaGetLastError();                                                                  \
+  }
+  MBO_VP_CASE(1)
+  MBO_VP_CASE(2)
+  MBO_VP_CASE(3)
+#undef MBO_VP_CASE
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -489,6 +647,9 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx) {
   template cudaError_t launch_axis<R>(AxisMode, int, const Geom&, const Tables<R>&, void*,     \
                                       const StatsPtrs&, int, int, cudaStream_t);               \
   template cudaError_t launch_project<R>(const Geom&, const R*, R*, int8_t*, double,          \
-                                         cudaStream_t);
+                                         cudaStream_t);                                        \
+  template cudaError_t launch_volume<R>(int, const Geom&, const R*, R*, unsigned long long*,   \
+                                        SelectState*, const StatsPtrs&, double, int,           \
+                                        cudaStream_t);
 
 }  // namespace mbo

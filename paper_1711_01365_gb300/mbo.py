@@ -28,7 +28,8 @@ STATUS = {0: "MBO_OK", 1: "MBO_ERR_INVALID_ARG", 2: "MBO_ERR_UNSUPPORTED_SIZE", 
 
 EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project",
            "mbo_step", "mbo_lyapunov", "mbo_run_until_stationary", "mbo_profile_enable",
-           "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_batch_create", "mbo_batch_destroy",
+           "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_step_volume", "mbo_run_volume",
+           "mbo_batch_create", "mbo_batch_destroy",
            "mbo_batch_step", "mbo_batch_run", "mbo_batch_workspace_bytes", "mbo_batch_last_error",
            "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
 
@@ -90,6 +91,9 @@ def lib():
     L.mbo_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_diffuse_noalloc.argtypes = [C.c_int, i64p, C.c_int, C.c_double, C.c_int, vp, vp, vp]
+    L.mbo_step_volume.argtypes = [vp, vp, C.c_int64, C.POINTER(mbo_stats), vp]
+    L.mbo_run_volume.argtypes = [vp, vp, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.mbo_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), i64p,
                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int,
                                    C.POINTER(mbo_config)]
@@ -109,7 +113,8 @@ def lib():
     L.mbo_last_error.restype = C.c_char_p
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
               "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
-              "mbo_diffuse_noalloc", "mbo_batch_create", "mbo_batch_destroy", "mbo_batch_step",
+              "mbo_diffuse_noalloc", "mbo_step_volume", "mbo_run_volume", "mbo_batch_create",
+              "mbo_batch_destroy", "mbo_batch_step",
               "mbo_batch_run"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -210,6 +215,24 @@ def mbo_diffuse_noalloc(dims, n: int, tau: float, dtype: int, A, A_tilde, stream
     d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
     _check(lib().mbo_diffuse_noalloc(len(dims), d, int(n), float(tau), int(dtype), _ptr(A),
                                      _ptr(A_tilde), _stream(stream)))
+
+
+def mbo_step_volume(h, A, n_plus: int = -1, want_stats: bool = False, stream=None):
+    st = mbo_stats()
+    _check(lib().mbo_step_volume(h, _ptr(A), int(n_plus), C.byref(st) if want_stats else None,
+                                 _stream(stream)), h)
+    return st.as_dict() if want_stats else None
+
+
+def mbo_run_volume(h, A, n_plus: int, max_steps: int, tol: float, stream=None) -> dict:
+    steps = C.c_int(0)
+    stat = C.c_int(0)
+    en = np.zeros(max_steps + 1, dtype=np.float64)
+    _check(lib().mbo_run_volume(h, _ptr(A), int(n_plus), int(max_steps), float(tol), C.byref(steps),
+                                C.byref(stat), en.ctypes.data_as(C.POINTER(C.c_double)),
+                                _stream(stream)), h)
+    s = steps.value
+    return {"steps": s, "stationary": bool(stat.value), "energies": en[: s + 1]}
 
 
 def mbo_profile_enable(h, enable: bool = True) -> None:
@@ -364,3 +387,9 @@ class Mbo:
 
     def run(self, A, max_steps: int, tol: float, stream=None) -> dict:
         return mbo_run_until_stationary(self.h, A, max_steps, tol, stream)
+
+    def step_volume(self, A, n_plus: int = -1, want_stats=False, stream=None):
+        return mbo_step_volume(self.h, A, n_plus, want_stats, stream)
+
+    def run_volume(self, A, n_plus: int, max_steps: int, tol: float, stream=None) -> dict:
+        return mbo_run_volume(self.h, A, n_plus, max_steps, tol, stream)
