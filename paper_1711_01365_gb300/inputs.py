@@ -23,6 +23,8 @@ experiments, Sec. 6.1, at the sizes the benchmark configurations name):
                       ~ exp(-|k|^2 / kc^2), some points replaced by -Q with
                       Q Haar in SO(3) (determinant -1).
   * ``batch_mixed``   many independent 2-D fields of uneven sizes and orders.
+  * ``paper_experiment`` the analytic initial fields of the paper's flat-torus
+                      experiments (Sec. 6.1 examples 1-3, Sec. 7).
 """
 from __future__ import annotations
 
@@ -163,6 +165,43 @@ def smooth_so3(dims, seed: int, kc: float = 32.0, frac_reflect: float = 0.2,
     if cnt:
         R[:, mask] = (-haar_so3(cnt, g).reshape(cnt, 9).T).astype(dtype)
     return R.reshape((9,) + shape)
+
+
+def paper_experiment(k: int, N: int = 1024):
+    """Initial fields of the flat-torus experiments of Sec. 6.1 (k = 1, 2, 3) and
+    of the volume-preserving flat-torus experiment of Sec. 7 (k = 4, the field
+    of k = 1).  Domain [-1/2, 1/2)^2 sampled at x = i/N - 1/2 (x fastest),
+    n = 2.  Inside the region named in the paper the matrix is the rotation by
+    alpha, elsewhere the reflection [[cos a, sin a], [sin a, -cos a]].
+    Returns (field (4, N, N), n, tau).  The paper gives tau = 8 dx or 64 dx
+    with dx = 1/1024; those values are read as the time of a heat kernel with
+    Fourier multiplier exp(-tau |xi|^2) for integer frequencies xi (a
+    2 pi-periodic length scale), i.e. tau / (4 pi^2) for the unit torus used
+    here.  Taken literally on the unit torus, tau = 64 dx spreads the kernel
+    over a third of the domain and examples 2 and 3 collapse to one phase
+    within a few steps, unlike the evolution the paper describes."""
+    c = np.arange(N) / N - 0.5
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    if k in (1, 4):
+        alpha = 0.5 * np.pi * np.sin(2 * np.pi * (X + Y))
+        r = np.sqrt(X * X + Y * Y)
+        th = np.arctan2(Y, X)
+        inside = r < 0.3 + 0.06 * np.sin(6 * th)
+        tau = 8.0 / 1024 / (4 * np.pi ** 2)
+    elif k in (2, 3):
+        alpha = np.pi * np.sin(2 * np.pi * Y) if k == 2 else 2 * np.pi * Y
+        w = 0.25 * np.abs(np.sin(2.5 * np.pi * Y))
+        inside = (X > w + 0.2) | (X < -w - 0.2)
+        tau = 64.0 / 1024 / (4 * np.pi ** 2)
+    else:
+        raise ValueError(k)
+    ca, sa = np.cos(alpha), np.sin(alpha)
+    F = np.empty((4, N, N))
+    F[0] = ca
+    F[1] = np.where(inside, -sa, sa)
+    F[2] = sa
+    F[3] = np.where(inside, ca, -ca)
+    return F, 2, tau
 
 
 # Batched 2-D workload: field i gets N = SIZES[i % 7], n = 2 + (i % 2), tau = 4 / N^2.
