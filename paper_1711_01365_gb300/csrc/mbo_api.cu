@@ -23,7 +23,9 @@ size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback) {
   if (fallback) b += (size_t)kFallbackCap * ((size_t)g.C * sizeof(float) + sizeof(int));
   return (b + 15) & ~(size_t)15;
 }
-size_t axis_smem_bytes(int len, int tx, size_t elem_bytes) { return (size_t)len * tx * 2 * elem_bytes; }
+size_t axis_smem_bytes(int len, int tx, size_t elem_bytes) {
+  return (size_t)row_pad(len) * tx * 2 * elem_bytes;
+}
 
 bool factor23(int64_t N, int& a, int& b) {
   a = b = 0;
@@ -70,6 +72,9 @@ Plan make_plan(int N) {
     s.dnr = make_div((unsigned)(N / rad[i]));
     s.tw = tw;
     if (s.m > 1) tw += s.m * (s.rad - 1);
+    // affine padded addressing: m a multiple of 8 (p/8 advances by m/8 per j), or
+    // the whole butterfly inside one 8-aligned block (lb divides 8)
+    s.pstride = (s.m % 8 == 0) ? s.m + s.m / 8 : ((s.lb <= 8 && 8 % s.lb == 0) ? s.m : 0);
     lb /= rad[i];
   }
   return p;

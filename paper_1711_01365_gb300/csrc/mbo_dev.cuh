@@ -133,31 +133,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layouts of M sequences of length N.
-//   RowLayout: sequence m at m*S, element p at p + p/16 (one pad slot per 16
-//              elements keeps short-span butterflies free of bank conflicts);
-//              butterflies map sequence-major (consecutive threads, consecutive j).
-//   ColLayout: element (m, p) at row p (swizzled, see addr) column m of a tile
-//              of M = 2^ltx adjacent columns;
-//              butterflies map column-fastest.
+// Shared-memory layouts of M sequences of length N.  Both pad one slot per 8
+// along the transformed axis: element p of a sequence sits at
+// phi(p) = p + p/8.  That keeps the strided butterfly accesses free of bank
+// conflicts and, for every stage whose span m is a multiple of 8 or whose
+// block length divides 8, makes phi(base + j*m) = phi(base) + j*pstride (see
+// Stage::pstride), so a butterfly addresses its RAD elements with one add
+// each.
+//   RowLayout: sequence m at m*S (S = row_pad(N)); butterflies map
+//              sequence-major (consecutive threads, consecutive positions).
+//   ColLayout: element (m, p) at row phi(p), column m of a tile of M = 2^ltx
+//              adjacent columns; butterflies map column-fastest.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int row_pad(int N) { return N + (N >> 4) + 1; }
+__host__ __device__ __forceinline__ int pad8(int p) { return p + (p >> 3); }
+__host__ __device__ __forceinline__ int row_pad(int N) { return N + (N >> 3) + 1; }
 
 struct RowLayout {
   static constexpr bool kColumns = false;
   int S;
-  __device__ __forceinline__ int addr(int m, int p) const { return m * S + p + (p >> 4); }
+  __device__ __forceinline__ int at(int m, int q) const { return m * S + q; }  // q = phi(p)
+  __device__ __forceinline__ int addr(int m, int p) const { return at(m, pad8(p)); }
 };
 struct ColLayout {
   static constexpr bool kColumns = true;
   int ltx;
-  int swz;  // 1 when the axis length is even (the swizzle pairs rows 2k, 2k+1), else 0
-  // Row p of the tile is stored at row p ^ b, b = bit 0 of (p >> 3) ^ (p >> 4):
-  // butterflies of the short-span stages, whose rows are 8 or 16 apart, then
-  // alternate between the two 64-byte halves of a 128-byte bank line.
-  __device__ __forceinline__ int addr(int m, int p) const {
-    return ((p ^ (((p >> 3) ^ (p >> 4)) & swz)) << ltx) + m;
-  }
+  __device__ __forceinline__ int at(int m, int q) const { return (q << ltx) + m; }
+  __device__ __forceinline__ int addr(int m, int p) const { return at(m, pad8(p)); }
 };
 
 // In-place mixed-radix transforms.  The forward transform is a decimation-in-
@@ -168,13 +169,18 @@ struct ColLayout {
 // butterfly reads and writes the same RAD slots, so threads never hold more
 // than one butterfly and a stage needs only a barrier after it.  Multiplier
 // tables are permuted on the host to the digit-reversed positions.
+//
+// Stage st works on blocks of length lb = N / (r_0 ... r_{st-1}); a butterfly
+// (block b, offset n1 < m = lb / RAD) owns positions b*lb + n1 + m*j.  Its
+// twiddles exp(-2 pi i n1 j / lb) come from the stage table [j - 1][n1].
 template <int DIR, int RAD, typename V, class L>
 __device__ __forceinline__ void radix_stage(V* s, const L& lay, int N, int M, const Stage& sd,
                                             const V* __restrict__ tw) {
   const int NR = N / RAD;
-  const int m = sd.m, lb = sd.lb;
+  const int m = sd.m, lb = sd.lb, ps = sd.pstride;
   const unsigned B = (unsigned)(NR * M);
   const V* __restrict__ tws = tw + sd.tw;
+  const int da = lay.at(0, ps);  // the affine stride in layout units
   for (unsigned u = threadIdx.x; u < B; u += blockDim.x) {
     int seq, w;
     if constexpr (L::kColumns) {
@@ -187,9 +193,18 @@ __device__ __forceinline__ void radix_stage(V* s, const L& lay, int N, int M, co
     const int b = (int)fdiv(sd.dm, (unsigned)w);
     const int n1 = w - b * m;
     const int base = b * lb + n1;
+    int a[RAD];
+    if (ps) {
+      const int a0 = lay.addr(seq, base);
+#pragma unroll
+      for (int j = 0; j < RAD; ++j) a[j] = a0 + j * da;
+    } else {
+#pragma unroll
+      for (int j = 0; j < RAD; ++j) a[j] = lay.addr(seq, base + j * m);
+    }
     V v[RAD];
 #pragma unroll
-    for (int j = 0; j < RAD; ++j) v[j] = s[lay.addr(seq, base + j * m)];
+    for (int j = 0; j < RAD; ++j) v[j] = s[a[j]];
     if (DIR < 0) {
       dft<-1, RAD>(v);
       if (m > 1) {
@@ -210,7 +225,7 @@ __device__ __forceinline__ void radix_stage(V* s, const L& lay, int N, int M, co
       dft<+1, RAD>(v);
     }
 #pragma unroll
-    for (int j = 0; j < RAD; ++j) s[lay.addr(seq, base + j * m)] = v[j];
+    for (int j = 0; j < RAD; ++j) s[a[j]] = v[j];
   }
   __syncthreads();
 }

@@ -28,6 +28,7 @@ struct FastDiv {
 // entries), in the axis twiddle table (unused when m == 1).
 struct Stage {
   int rad, lb, m, tw;
+  int pstride;  // p -> p + p/8 maps base + j*m to phi(base) + j*pstride (0: not affine)
   FastDiv dm;   // division by m
   FastDiv dnr;  // division by N / rad
 };

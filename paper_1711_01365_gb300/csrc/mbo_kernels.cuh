@@ -290,7 +290,7 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   const int o = rem / xt;
   const int x0 = (rem - o * xt) << ltx;
   V* base = W + (long long)q * g.P + (long long)o * ostride + x0;
-  const ColLayout lay{ltx, (L & 1) ? 0 : 1};
+  const ColLayout lay{ltx};
   const int T = blockDim.x, tid = threadIdx.x;
   const V* tw = static_cast<const V*>(t.tw[axis]);
 
