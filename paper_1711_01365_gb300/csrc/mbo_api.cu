@@ -52,6 +52,7 @@ FastDiv make_div(unsigned d) {
 // Stage twiddle offsets are assigned in stage order.
 Plan make_plan(int N) {
   Plan p{};
+  p.len = N;
   int a, b;
   factor23(N, a, b);
   int rad[kMaxStages];
@@ -80,7 +81,20 @@ Plan make_plan(int N) {
   return p;
 }
 
+Plan axis_plan(const Geom& g, int axis, bool f32) {
+  const int N = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
+  if (f32 && warp_plan_length(N) && (axis == 0 || warp_tile(N, g.nx, 8) != 0) &&
+      (axis == 0 || axis < g.ndim)) {
+    Plan p{};
+    p.len = N;
+    p.lq = N == 1024 ? 32 : 16;
+    return p;
+  }
+  return make_plan(N);
+}
+
 int plan_twiddles(const Plan& p) {
+  if (p.lq) return p.len;
   int n = 0;
   for (int i = 0; i < p.nst; ++i)
     if (p.st[i].m > 1) n += p.st[i].m * (p.st[i].rad - 1);
@@ -90,6 +104,10 @@ int plan_twiddles(const Plan& p) {
 // pos[k]: digit-reversed position where the forward network leaves frequency k.
 void digit_positions(const Plan& p, int N, std::vector<int>& pos) {
   pos.assign(N, 0);
+  if (p.lq) {  // warp-cooperative plans leave the spectrum in natural order
+    for (int k = 0; k < N; ++k) pos[k] = k;
+    return;
+  }
   for (int k = 0; k < N; ++k) {
     int kk = k, len = N, off = 0;
     for (int st = 0; st < p.nst; ++st) {
@@ -208,7 +226,7 @@ void build_tables(mbo_ctx* h, TabBuild<R>& tb, Tables<R>& t) {
   };
   for (int ax = 0; ax < 3; ++ax) {
     const int N = lens[ax];
-    t.plan[ax] = make_plan(N);
+    t.plan[ax] = axis_plan(h->g, ax, sizeof(R) == 4);
     tb.off_tw[ax] = reserve((size_t)std::max(plan_twiddles(t.plan[ax]), 1) * 2 * sizeof(R));
     tb.off_g[ax] = reserve((size_t)N * sizeof(R));
     tb.off_om[ax] = reserve((size_t)N * sizeof(R));
@@ -219,6 +237,17 @@ void build_tables(mbo_ctx* h, TabBuild<R>& tb, Tables<R>& t) {
     const int N = lens[ax];
     const Plan& pl = t.plan[ax];
     R* tw = reinterpret_cast<R*>(&tb.bytes[tb.off_tw[ax]]);
+    if (pl.lq) {  // [k2][l] = exp(-2 pi i l k2 / N)
+      const int E = N / pl.lq;
+      for (int k2 = 0; k2 < E; ++k2)
+        for (int l = 0; l < pl.lq; ++l) {
+          const long long e = ((long long)l * k2) % N;
+          const double ang = 2.0 * pi * (double)e / (double)N;
+          const size_t i = (size_t)k2 * pl.lq + l;
+          tw[2 * i] = (R)std::cos(ang);
+          tw[2 * i + 1] = (R)(-std::sin(ang));
+        }
+    }
     for (int st = 0; st < pl.nst; ++st) {
       const Stage& s = pl.st[st];
       if (s.m <= 1) continue;
@@ -478,8 +507,19 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     }
     h->axis_threads = c.axis_threads;
   }
-  const size_t rs = row_smem_bytes(g, h->elem, true);
-  const size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
+  size_t rs = row_smem_bytes(g, h->elem, true);
+  size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
+  int min_tx = h->tx;  // narrowest column tile of any strided pass
+  if (dtype == MBO_F32) {
+    if (axis_plan(g, 0, true).lq) rs = std::max(rs, wrow_smem_bytes(g, g.nx, true));
+    for (int ax = 1; ax < ndim; ++ax) {
+      const int L = ax == 1 ? g.ny : g.nz;
+      if (!axis_plan(g, ax, true).lq) continue;
+      const int wt = warp_tile(L, g.nx, h->tx);
+      as = std::max(as, wcol_smem_bytes(L, wt));
+      min_tx = std::min(min_tx, wt);
+    }
+  }
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
   if (rs > (size_t)maxsm || as > (size_t)maxsm) {
@@ -497,7 +537,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   };
   const size_t wbytes = (size_t)g.Q * (size_t)g.P * 2 * h->elem;
   const int rows = g.nz * g.ny;
-  const int tiles = g.Q * std::max(g.nz, g.ny) * (g.nx / h->tx);
+  const int tiles = g.Q * std::max(g.nz, g.ny) * (g.nx / min_tx);
   const size_t nparts = (size_t)std::max(rows, tiles);
   h->ngroups = (nparts + kReduceGroup - 1) / kReduceGroup;
   if (!alloc(&h->W, wbytes) ||
@@ -527,8 +567,8 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     cudaMemcpy(h->tabs, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice);
     bind_tables(h, tb, h->td);
   }
-  const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tx)
-                                          : prepare_kernels<double>(g, h->tx);
+  const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx)
+                                          : prepare_kernels<double>(g, h->td, h->tx);
   if (pe != cudaSuccess) {
     mbo_destroy(h);
     return MBO_ERR_CUDA;

@@ -22,9 +22,19 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-// multiply by DIR*i (DIR = -1: -i, DIR = +1: +i)
-template <int DIR, typename V> __device__ __forceinline__ V cmul_i(V a) {
-  return DIR < 0 ? V{a.y, -a.x} : V{-a.y, a.x};
+// a + DIR*i*t and a - DIR*i*t, lane by lane (the swap of t's parts costs
+// nothing in scalar form).
+template <int DIR, typename V> __device__ __forceinline__ V cadd_i(V a, V t) {
+  return DIR < 0 ? V{a.x + t.y, a.y - t.x} : V{a.x - t.y, a.y + t.x};
+}
+template <int DIR, typename V> __device__ __forceinline__ V csub_i(V a, V t) {
+  return DIR < 0 ? V{a.x - t.y, a.y + t.x} : V{a.x + t.y, a.y - t.x};
+}
+// FP32 complex add and subtract as one packed two-lane instruction each
+// (sm_100 family); the same IEEE operations lane by lane as the scalar forms.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
 // ---------------------------------------------------------------------------
@@ -42,19 +52,19 @@ template <int DIR, typename V> __device__ __forceinline__ void dft3(V* v) {
   V s = cadd(v[1], v[2]);
   V d = csub(v[1], v[2]);
   V t1 = V{v[0].x - R(0.5) * s.x, v[0].y - R(0.5) * s.y};
-  V t2 = cmul_i<DIR>(V{h * d.x, h * d.y});
+  const V hd = V{h * d.x, h * d.y};
   v[0] = cadd(v[0], s);
-  v[1] = cadd(t1, t2);
-  v[2] = csub(t1, t2);
+  v[1] = cadd_i<DIR>(t1, hd);
+  v[2] = csub_i<DIR>(t1, hd);
 }
 
 template <int DIR, typename V> __device__ __forceinline__ void dft4(V* v) {
   V s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-  V s13 = cadd(v[1], v[3]), d13 = cmul_i<DIR>(csub(v[1], v[3]));
+  V s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
   v[0] = cadd(s02, s13);
   v[2] = csub(s02, s13);
-  v[1] = cadd(d02, d13);
-  v[3] = csub(d02, d13);
+  v[1] = cadd_i<DIR>(d02, d13);
+  v[3] = csub_i<DIR>(d02, d13);
 }
 
 template <int DIR, typename V> __device__ __forceinline__ void dft8(V* v) {
@@ -66,12 +76,16 @@ template <int DIR, typename V> __device__ __forceinline__ void dft8(V* v) {
   dft4<DIR>(o);
   // W8^k = exp(DIR 2 pi i k / 8)
   o[1] = cmul(o[1], V{c, R(DIR) * c});
-  o[2] = cmul_i<DIR>(o[2]);
   o[3] = cmul(o[3], V{-c, R(DIR) * c});
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    v[k] = cadd(e[k], o[k]);
-    v[k + 4] = csub(e[k], o[k]);
+    if (k == 2) {  // W8^2 = DIR*i
+      v[2] = cadd_i<DIR>(e[2], o[2]);
+      v[6] = csub_i<DIR>(e[2], o[2]);
+    } else {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
   }
 }
 
@@ -92,14 +106,18 @@ template <int DIR, typename V> __device__ __forceinline__ void dft16(V* v) {
   o[1] = cmul(o[1], V{c1, D * s1});
   o[2] = cmul(o[2], V{c2, D * c2});
   o[3] = cmul(o[3], V{s1, D * c1});
-  o[4] = cmul_i<DIR>(o[4]);
   o[5] = cmul(o[5], V{-s1, D * c1});
   o[6] = cmul(o[6], V{-c2, D * c2});
   o[7] = cmul(o[7], V{-c1, D * s1});
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    v[k] = cadd(e[k], o[k]);
-    v[k + 8] = csub(e[k], o[k]);
+    if (k == 4) {  // W16^4 = DIR*i
+      v[4] = cadd_i<DIR>(e[4], o[4]);
+      v[12] = csub_i<DIR>(e[4], o[4]);
+    } else {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 8] = csub(e[k], o[k]);
+    }
   }
 }
 

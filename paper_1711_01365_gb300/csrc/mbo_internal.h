@@ -33,9 +33,17 @@ struct Stage {
   FastDiv dnr;  // division by N / rad
 };
 
-// Radix plan of one axis: forward stages applied in order, product = N.
+// Transform plan of one axis.
+//   lq == 0: the in-place network of nst stages (forward stages applied in
+//            order, product = N); the spectrum is left digit-reversed.
+//   lq >  0: the warp-cooperative four-step transform of N = lq * (N / lq)
+//            points held in registers by lq lanes per sequence; the spectrum
+//            is in natural order and the twiddle table holds
+//            exp(-2 pi i l k2 / N) at [k2][l] (k2 < N / lq, l < lq).
 struct Plan {
   int nst;
+  int lq;
+  int len;  // N
   Stage st[kMaxStages];
 };
 
@@ -75,7 +83,8 @@ struct Geom {
 template <typename R> struct Tables {
   const void* tw[3];   // per-stage twiddles of each axis (see Stage::tw)
   const R* g[3];       // exp(-4 pi^2 tau k^2), k the signed frequency held at each
-                       // digit-reversed spectrum position of the forward transform
+                       // spectrum position of the forward transform (digit-reversed
+                       // or natural, per the axis plan)
   const R* om[3];      // 1 - g at the same positions (computed as -expm1)
   Plan plan[3];
   R inv_p;             // 1 / P, folded into the multiplier
@@ -136,10 +145,24 @@ cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
 bool factor23(int64_t N, int& a, int& b);
 FastDiv make_div(unsigned d);
 Plan make_plan(int N);
+// Plan of one axis of a geometry: the warp-cooperative plan (FP32, lengths
+// 256, 512, 1024; strided axes need nx % 4 == 0) where one exists, else make_plan.
+Plan axis_plan(const Geom& g, int axis, bool f32);
 int plan_twiddles(const Plan& p);
 int pick_tx(int nx, int cap);
 
-template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx);
+// FP32 passes over warp-plan axes (k_warp.cu).
+bool warp_plan_length(int N);
+int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4 or 8; 0: none)
+size_t wrow_smem_bytes(const Geom& g, int N, bool fallback);
+size_t wcol_smem_bytes(int L, int tx);
+cudaError_t launch_wrow(RowMode mode, const Geom& g, const Tables<float>& t, const float* A_in,
+                        float* A_out, void* W, const StatsPtrs& sp, double fallback_sigma,
+                        cudaStream_t s, bool prepare_only);
+cudaError_t launch_wcol(AxisMode mode, int axis, const Geom& g, const Tables<float>& t, void* W,
+                        const StatsPtrs& sp, int tx, cudaStream_t s, bool prepare_only);
+
+template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& t, int tx);
 template <typename R>
 cudaError_t launch_volume(int which, const Geom& g, const R* At, R* A, unsigned long long* keys,
                           SelectState* ss, const StatsPtrs& sp, double fb, int blocks,

@@ -71,11 +71,11 @@ __device__ __forceinline__ R project_point_f64(const R* m, R* b) {
 }
 
 // Record a projected point: compare with the old field, write the new value
-// to global memory and (packed) to the shared row.
+// to global memory and, packed, to shared memory (plane q at dst[q * qstride]).
 template <int NM, typename R, typename V>
 __device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, long long off, int x,
-                                             const R* old, const R* b, R sg, V* s,
-                                             const RowLayout& lay, PointStats<R>& ps) {
+                                             const R* old, const R* b, R sg, V* dst, int qstride,
+                                             PointStats<R>& ps) {
   constexpr int C = NM * NM, Q = (C + 1) / 2;
   R d = R(0), nb = R(0);
 #pragma unroll
@@ -89,7 +89,7 @@ __device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, lon
 #pragma unroll
   for (int c = 0; c < C; ++c) A[c * P + off + x] = b[c];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) s[lay.addr(q, x)] = V{b[2 * q], (2 * q + 1 < C) ? b[2 * q + 1] : R(0)};
+  for (int q = 0; q < Q; ++q) dst[q * qstride] = V{b[2 * q], (2 * q + 1 < C) ? b[2 * q + 1] : R(0)};
 }
 
 // Reduce a block's point statistics and, in the last block of the grid,
@@ -237,7 +237,7 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
       sg = project_point_f64<NM>(m, b);
       ps.fallback += 1;
     }
-    finish_point<NM>(A, P, off, x, old, b, sg, s, lay, ps);
+    finish_point<NM>(A, P, off, x, old, b, sg, s + lay.addr(0, x), lay.S, ps);
   }
   if (is_f32 && NM >= 2) {
     __syncthreads();
@@ -252,7 +252,7 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
       }
       const R sg = project_point_f64<NM>(m, b);
       ps.fallback += 1;
-      finish_point<NM>(A, P, off, x, old, b, sg, s, lay, ps);
+      finish_point<NM>(A, P, off, x, old, b, sg, s + lay.addr(0, x), lay.S, ps);
     }
   }
   __syncthreads();
@@ -549,6 +549,9 @@ template <typename R>
 cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R* A_in, R* A_out,
                        void* W, const StatsPtrs& sp, double fallback_sigma, int threads,
                        cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (t.plan[0].lq) return launch_wrow(mode, g, t, A_in, A_out, W, sp, fallback_sigma, s, false);
+  }
   const R fb = (R)fallback_sigma;
 #define MBO_ROW_CASE(NM)                                                                   \
   if (g.n == NM) {                                                                         \
@@ -587,6 +590,9 @@ static cudaError_t launch_axis_m(const Geom& g, const Tables<R>& t, void* W, con
 template <typename R>
 cudaError_t launch_axis(AxisMode mode, int axis, const Geom& g, const Tables<R>& t, void* W,
                         const StatsPtrs& sp, int tx, int threads, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (t.plan[axis].lq) return launch_wcol(mode, axis, g, t, W, sp, tx, s, false);
+  }
   switch (mode) {
     case AXIS_FWD: return launch_axis_m<R, AXIS_FWD>(g, t, W, sp, axis, tx, threads, s);
     case AXIS_INV: return launch_axis_m<R, AXIS_INV>(g, t, W, sp, axis, tx, threads, s);
@@ -611,10 +617,21 @@ cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
 // Raise the shared-memory limit of every kernel a geometry uses, without
 // launching (so that later launches inside stream capture make no attribute
 // call).
-template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx) {
+template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& tabs, int tx) {
   Tables<R> t{};
   StatsPtrs sp{};
   cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(R) == 4) {
+    if (tabs.plan[0].lq) {
+      for (int m = ROW_FWD; m <= ROW_INV_PROJECT_FWD && e == cudaSuccess; ++m)
+        e = launch_wrow((RowMode)m, g, tabs, nullptr, nullptr, nullptr, sp, 0.0, 0, true);
+    }
+    for (int axis = 1; axis <= (g.ndim == 3 ? 2 : 1) && e == cudaSuccess; ++axis) {
+      if (!tabs.plan[axis].lq) continue;
+      for (int m = AXIS_FWD; m <= AXIS_ENERGY && e == cudaSuccess; ++m)
+        e = launch_wcol((AxisMode)m, axis, g, tabs, nullptr, sp, tx, 0, true);
+    }
+  }
 #define MBO_PREP_ROW(NM)                                                                       \
   if (g.n == NM) {                                                                             \
     if (e == cudaSuccess)                                                                      \
@@ -641,7 +658,7 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, int tx) {
 }
 
 #define MBO_INSTANTIATE(R)                                                                     \
-  template cudaError_t prepare_kernels<R>(const Geom&, int);                                   \
+  template cudaError_t prepare_kernels<R>(const Geom&, const Tables<R>&, int);                 \
   template cudaError_t launch_row<R>(RowMode, const Geom&, const Tables<R>&, const R*, R*,     \
                                      void*, const StatsPtrs&, double, int, cudaStream_t);      \
   template cudaError_t launch_axis<R>(AxisMode, int, const Geom&, const Tables<R>&, void*,     \

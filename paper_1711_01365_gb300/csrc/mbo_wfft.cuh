@@ -1,0 +1,136 @@
+// Warp-cooperative four-step transforms for FP32 axes of length 256, 512 and
+// 1024 (the diffusion of Sec. 5.1 of Osting & Wang, arXiv:1711.01365, along
+// one axis).
+//
+// A sequence of N = LQ * E points is held by LQ lanes, E points each: lane l
+// holds a[l + LQ j] in register j.  The forward transform
+//   X[k] = sum_x a[x] exp(-2 pi i x k / N)
+// factors with x = x1 + LQ x2 and k = k2 + E k1 as
+//   X[k2 + E k1] = sum_x1 W_LQ^(x1 k1) W_N^(x1 k2) sum_x2 a[x1 + LQ x2] W_E^(x2 k2)
+// (W_M = exp(-2 pi i / M)): a length-E DFT in each lane's registers, one
+// twiddle per register, a transpose through the warp's own shared-memory
+// region, and length-LQ DFTs in registers again.  The spectrum comes out in
+// natural order with lane l holding X[l + LQ j] in register j -- the layout the
+// inverse transform takes as input -- so a forward transform, a multiplier
+// and an inverse transform run on registers with no block barrier.  The
+// transposes need only __syncwarp.
+#pragma once
+#include "mbo_dev.cuh"
+
+namespace mbo {
+
+// cos(pi j / 16) for any integer j.
+__host__ __device__ constexpr double cos_pi16(int j) {
+  j = ((j % 32) + 32) % 32;
+  const int a = j <= 16 ? j : 32 - j;  // cos(pi a / 16), 0 <= a <= 16
+  const int b = a <= 8 ? a : 16 - a;   // |cos| = cos(pi b / 16), 0 <= b <= 8
+  const double c = b == 0   ? 1.0
+                   : b == 1 ? 0.98078528040323044913
+                   : b == 2 ? 0.92387953251128675613
+                   : b == 3 ? 0.83146961230254523708
+                   : b == 4 ? 0.70710678118654752440
+                   : b == 5 ? 0.55557023301960222474
+                   : b == 6 ? 0.38268343236508977173
+                   : b == 7 ? 0.19509032201612826785
+                            : 0.0;
+  return a <= 8 ? c : -c;
+}
+
+// a * W^j with W = exp(DIR 2 pi i / 32); j is a constant after unrolling.
+template <int DIR, typename V> __device__ __forceinline__ V twiddle32(V a, int j) {
+  using R = decltype(a.x);
+  j &= 31;
+  if (j == 0) return a;
+  if (j == 8) return DIR < 0 ? V{a.y, -a.x} : V{-a.y, a.x};
+  if (j == 16) return V{-a.x, -a.y};
+  if (j == 24) return DIR < 0 ? V{-a.y, a.x} : V{a.y, -a.x};
+  const R c = (R)cos_pi16(j), s = (R)(DIR * cos_pi16(j - 8));
+  return V{a.x * c - a.y * s, a.x * s + a.y * c};
+}
+
+// Length-32 DFT in registers, natural order in and out: 32 = 4 x 8 with
+// n = n1 + 8 n2, k = k2 + 4 k1 (length-4 DFTs over n2, twiddles W32^(n1 k2),
+// length-8 DFTs over n1).
+template <int DIR, typename V> __device__ __forceinline__ void dft32(V* v) {
+  V u[8][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 8; ++n1) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) u[n1][n2] = v[n1 + 8 * n2];
+    dft4<DIR>(u[n1]);
+#pragma unroll
+    for (int k2 = 1; k2 < 4; ++k2) u[n1][k2] = twiddle32<DIR>(u[n1][k2], n1 * k2);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    V w[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) w[n1] = u[n1][k2];
+    dft8<DIR>(w);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) v[k2 + 4 * k1] = w[k1];
+  }
+}
+
+template <int DIR, int LEN, typename V> __device__ __forceinline__ void rdft(V* v) {
+  if constexpr (LEN == 32) dft32<DIR>(v);
+  else dft<DIR, LEN>(v);
+}
+
+template <int N, int LQ> struct WarpFFT {
+  static constexpr int E = N / LQ;         // points per lane
+  static constexpr int G = E / LQ;         // length-LQ DFTs per lane in the second step
+  static constexpr int RS = (LQ + 1) * E;  // transpose region of one sequence (complex)
+  static_assert(E % LQ == 0 && (E == 16 || E == 32) && (LQ == 16 || LQ == 32),
+                "supported shapes: 16x16, 16x32, 32x32");
+
+  // v[j] = a[l + LQ j]  ->  v[j] = X[l + LQ j].  buf: the sequence's RS slots;
+  // tw[k2 * LQ + l] = W_N^(l k2).
+  template <typename V>
+  __device__ __forceinline__ static void fwd(V (&v)[E], V* buf, const V* __restrict__ tw, int l) {
+    rdft<-1, E>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], __ldg(&tw[k2 * LQ + l]));
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) buf[k2 * (LQ + 1) + l] = v[k2];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      V u[LQ];
+#pragma unroll
+      for (int x1 = 0; x1 < LQ; ++x1) u[x1] = buf[(l + LQ * r) * (LQ + 1) + x1];
+      rdft<-1, LQ>(u);
+#pragma unroll
+      for (int k1 = 0; k1 < LQ; ++k1) v[r + G * k1] = u[k1];
+    }
+    __syncwarp();
+  }
+
+  // v[j] = X[l + LQ j]  ->  v[j] = sum_k X[k] exp(+2 pi i (l + LQ j) k / N)
+  // (unnormalised): the forward steps transposed and conjugated, in reverse.
+  template <typename V>
+  __device__ __forceinline__ static void inv(V (&v)[E], V* buf, const V* __restrict__ tw, int l) {
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      V u[LQ];
+#pragma unroll
+      for (int k1 = 0; k1 < LQ; ++k1) u[k1] = v[r + G * k1];
+      rdft<+1, LQ>(u);
+#pragma unroll
+      for (int x1 = 0; x1 < LQ; ++x1) buf[(l + LQ * r) * (LQ + 1) + x1] = u[x1];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) v[k2] = buf[k2 * (LQ + 1) + l];
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) {
+      V c = __ldg(&tw[k2 * LQ + l]);
+      c.y = -c.y;
+      v[k2] = cmul(v[k2], c);
+    }
+    rdft<+1, E>(v);
+  }
+};
+
+}  // namespace mbo
