@@ -553,10 +553,11 @@ template <typename R> __device__ __forceinline__ R cofactor3(const R* X, R* C) {
 // X <- (X + X^{-t}) / 2 follow; each squares the distance to orthogonality
 // (d -> d^2 / 2) and their fixed point is exactly orthogonal.  det X keeps
 // the sign of det m.  est receives |det m| / |cof m|_F, which lies in
-// [sigma_min / sqrt(3), sigma_min]; callers route points with small est (and
-// exactly singular ones, where the iteration is undefined) elsewhere.
+// [sigma_min / sqrt(3), sigma_min]; points with est <= skip_below (exactly
+// singular ones, where the iteration is undefined, included) are returned
+// unprocessed for the caller to route elsewhere.
 template <int ITMAX, int NUN, typename R>
-__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est) {
+__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R skip_below = R(0)) {
   R X[9], C[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) X[k] = m[k];
@@ -568,7 +569,7 @@ __device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est) {
     for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
     est = fabs(det) * rsqrt_(nc);
   }
-  if (!(est > R(0))) {  // singular or not finite: caller's fallback
+  if (!(est > skip_below)) {  // singular, not finite or below the caller's limit: caller's fallback
 #pragma unroll
     for (int k = 0; k < 9; ++k) b[k] = X[k];
     return sg;
@@ -602,6 +603,103 @@ __device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est) {
   return sg;
 }
 
+// n = 3, FP32: the nearest matrix of the class sg (det = sg) through the
+// quaternion form of the problem (Horn 1987).  For a = sg m / |m|_F the
+// nearest rotation R(q) maximises tr(R^t a) = q^t K q over unit quaternions q,
+// K the symmetric traceless 4x4 matrix below, so q is the eigenvector of the
+// largest eigenvalue l1 = s1 + s2 + s3 (the singular values of a, the
+// smallest one signed by det a).  l1 is the largest root of
+//   p(l) = det(K - l I) = l^4 - 2 |a|^2 l^2 - 8 det(a) l + det K,
+// reached by Newton's method from the upper bound sqrt(3) |a|_F, and q is the
+// column of adj(K - l1 I) = prod_{i>1} (l_i - l1) q q^t with the largest
+// diagonal magnitude.  The other eigenvalues are s1 - s2 - s3, s2 - s1 - s3,
+// s3 - s1 - s2, so p'(l1) = 8 (s2 + s3)(s1 + s3)(s1 + s2): the eigenvector's
+// conditioning is that of the polar factor itself, 1 / (s2 + s3), and unlike
+// the Newton iteration nothing here inverts a; the rounding of l1, however,
+// enters q as eps / (s2 + s3)^2.  Returns p'(l1) / 32, a lower bound of
+// (s2 + s3) / |m|_F, for the caller's accuracy test.
+__device__ __forceinline__ float polar3_quat(const float* m, float sg, float* b) {
+  float n2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) n2 += m[k] * m[k];
+  const float sc = sg * rsqrtf(n2);
+  float a[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a[k] = m[k] * sc;
+  float na = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) na += a[k] * a[k];
+  const float adet = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  // K (symmetric, upper triangle)
+  const float k00 = a[0] + a[4] + a[8], k11 = a[0] - a[4] - a[8];
+  const float k22 = -a[0] + a[4] - a[8], k33 = -a[0] - a[4] + a[8];
+  const float k01 = a[7] - a[5], k02 = a[2] - a[6], k03 = a[3] - a[1];
+  const float k12 = a[1] + a[3], k13 = a[2] + a[6], k23 = a[5] + a[7];
+  // det K from the 2x2 minors of rows (0, 1) and rows (2, 3)
+  float c0;
+  {
+    const float t01 = k00 * k11 - k01 * k01, t02 = k00 * k12 - k02 * k01;
+    const float t03 = k00 * k13 - k03 * k01, t12 = k01 * k12 - k02 * k11;
+    const float t13 = k01 * k13 - k03 * k11, t23 = k02 * k13 - k03 * k12;
+    const float b01 = k02 * k13 - k12 * k03, b02 = k02 * k23 - k22 * k03;
+    const float b03 = k02 * k33 - k23 * k03, b12 = k12 * k23 - k22 * k13;
+    const float b13 = k12 * k33 - k23 * k13, b23 = k22 * k33 - k23 * k23;
+    c0 = t01 * b23 - t02 * b13 + t03 * b12 + t12 * b03 - t13 * b02 + t23 * b01;
+  }
+  const float c2 = -2.f * na, c1 = -8.f * adet;
+  float lam = sqrtf(3.f * na);
+#pragma unroll 1
+  for (int it = 0; it < 16; ++it) {
+    const float l2 = lam * lam;
+    const float p = fmaf(l2 + c2, l2, fmaf(c1, lam, c0));
+    const float dp = fmaf(lam, fmaf(4.f, l2, 2.f * c2), c1);
+    if (!(dp > 0.f)) break;
+    const float step = p / dp;
+    lam -= step;
+    if (fabsf(step) <= 1e-7f * lam) break;
+  }
+  const float dp = fmaf(lam, fmaf(4.f, lam * lam, 2.f * c2), c1);
+  // A = K - lam I; its 3x3 minors M(r, c) (symmetric), each expanded along
+  // the row that deleting r leaves alone in its pair.
+  const float a00 = k00 - lam, a11 = k11 - lam, a22 = k22 - lam, a33 = k33 - lam;
+  const float a01 = k01, a02 = k02, a03 = k03, a12 = k12, a13 = k13, a23 = k23;
+  const float t01 = a00 * a11 - a01 * a01, t02 = a00 * a12 - a02 * a01;
+  const float t03 = a00 * a13 - a03 * a01, t12 = a01 * a12 - a02 * a11;
+  const float t13 = a01 * a13 - a03 * a11;
+  const float b01 = a02 * a13 - a12 * a03, b02 = a02 * a23 - a22 * a03;
+  const float b03 = a02 * a33 - a23 * a03, b12 = a12 * a23 - a22 * a13;
+  const float b13 = a12 * a33 - a23 * a13, b23 = a22 * a33 - a23 * a23;
+  const float M00 = a11 * b23 - a12 * b13 + a13 * b12;
+  const float M11 = a00 * b23 - a02 * b03 + a03 * b02;
+  const float M22 = a03 * t13 - a13 * t03 + a33 * t01;
+  const float M33 = a02 * t12 - a12 * t02 + a22 * t01;
+  const float M01 = a01 * b23 - a12 * b03 + a13 * b02;
+  const float M02 = a01 * b13 - a11 * b03 + a13 * b01;
+  const float M03 = a01 * b12 - a11 * b02 + a12 * b01;
+  const float M12 = a00 * b13 - a01 * b03 + a03 * b01;
+  const float M13 = a00 * b12 - a01 * b02 + a02 * b01;
+  const float M23 = a03 * t12 - a13 * t02 + a23 * t01;
+  // adj = ((-1)^(i+j) M(i, j)); at l1 it is negative semidefinite: take the
+  // column of the most negative diagonal entry.
+  float w = M00, x = -M01, y = M02, z = -M03, best = M00;
+  if (M11 < best) { best = M11; w = -M01; x = M11; y = -M12; z = M13; }
+  if (M22 < best) { best = M22; w = M02; x = -M12; y = M22; z = -M23; }
+  if (M33 < best) { best = M33; w = -M03; x = M13; y = -M23; z = M33; }
+  const float ww = w * w, xx = x * x, yy = y * y, zz = z * z;
+  const float f = sg / (ww + xx + yy + zz);
+  b[0] = (ww + xx - yy - zz) * f;
+  b[1] = 2.f * (x * y - w * z) * f;
+  b[2] = 2.f * (x * z + w * y) * f;
+  b[3] = 2.f * (x * y + w * z) * f;
+  b[4] = (ww - xx + yy - zz) * f;
+  b[5] = 2.f * (y * z - w * x) * f;
+  b[6] = 2.f * (x * z - w * y) * f;
+  b[7] = 2.f * (y * z + w * x) * f;
+  b[8] = (ww - xx - yy + zz) * f;
+  return dp * (1.f / 32.f);
+}
+
 template <int NM, typename R> __device__ __forceinline__ R polar(const R* m, R* b, R& smin) {
   if constexpr (NM == 1) return polar1(m, b, smin);
   else if constexpr (NM == 2) return polar2(m, b, smin);
@@ -617,7 +715,7 @@ template <int NM> __device__ __forceinline__ double polar_f64(const double* m, d
 #pragma unroll
     for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
     double est = 0.0;
-    const double sg = polar3_newton<16, 3>(m, b, est);
+    const double sg = polar3_newton<16, 3>(m, b, est, 1e-12 * sqrt(nx));
     smin = est;
     if (est > 1e-12 * sqrt(nx)) return sg;
     return polar3(m, b, smin);

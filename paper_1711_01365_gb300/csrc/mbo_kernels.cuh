@@ -33,10 +33,18 @@ template <typename R> struct PointStats {
   int fallback = 0;
 };
 
+// The quaternion projection's accuracy bound (s2 + s3) / |m|_F >= kQuatGap
+// keeps its error (about 4e-7 / ((s2 + s3) / s1) in FP32) well inside the
+// FP32 step tolerance.
+constexpr float kQuatGap = 0.05f;
+
 // Project one point in the element type R.  Returns false when the point
-// must be re-projected in FP64 instead: FP32 points whose smallest singular
-// value is below fb (the configured threshold), and FP32 points singular to
-// single precision (always).  FP64 elements are always projected here.
+// must be re-projected in FP64 instead.  FP32, n = 3: the scaled Newton
+// iteration for points whose smallest singular value is at least fb (the
+// configured threshold) and not small to single precision; below that the
+// quaternion form, whose error grows with 1 / (s2 + s3) instead of 1 / s3;
+// FP64 only where s2 + s3 is small too.  FP32, n = 2: points whose smallest
+// singular value is below fb.  FP64 elements are always projected here.
 template <int NM, typename R>
 __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
   if constexpr (sizeof(R) == 8) {
@@ -48,8 +56,10 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
     float est = 0.f;
-    sg = polar3_newton<10, 2>(m, b, est);
-    return !(est < fb) && est > 1e-6f * sqrtf(nx);
+    const float lim = fmaxf(fb, 1e-6f * sqrtf(nx));
+    sg = polar3_newton<10, 2>(m, b, est, lim);
+    if (est > lim) return true;
+    return polar3_quat(m, sg, b) >= kQuatGap;
   } else {
     float sm;
     sg = polar<NM>(m, b, sm);
