@@ -22,8 +22,12 @@ namespace {
 __host__ __device__ constexpr int wrow_lq(int N) { return N == 1024 ? 32 : 16; }
 __host__ __device__ constexpr int wrow_rb(int N) { return N == 1024 ? 1 : 2; }  // rows per block: whole warps
 
+// Blocks per SM the register budget is sized for.
+__host__ __device__ constexpr int wrow_minb(int N) { return N > 0 ? 4 : 4; }
+__host__ __device__ constexpr int wcol_minb(int L, int TX) { return L > 0 && TX == 8 ? 2 : 3; }
+
 template <int NM, int MODE, int N>
-__global__ void __launch_bounds__(wrow_rb(N) * ((NM * NM + 1) / 2) * wrow_lq(N))
+__global__ void __launch_bounds__(wrow_rb(N) * ((NM * NM + 1) / 2) * wrow_lq(N), wrow_minb(N))
 k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2* W, StatsPtrs sp,
        float fb_sigma) {
   constexpr int LQ = wrow_lq(N), RB = wrow_rb(N);
@@ -72,7 +76,8 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     F::fwd(v, buf, tw, l);
     if (live) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) W[q * P + off + l + LQ * j] = v[j];
+      for (int j = 0; j < E; ++j)
+        if (q < Q - 1 || l + LQ * j < g.xh) W[q * P + off + l + LQ * j] = v[j];
     }
     if (sp.do_stats) {
       const double tot = block_sum(defect, redd);
@@ -82,9 +87,23 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     return;
   }
 
-  // inverse modes: the spectrum rows straight into registers (coalesced)
+  // inverse modes: the spectrum rows straight into registers (coalesced); a
+  // Hermitian last plane supplies columns k > N/2 as conj(column N - k)
+  const bool mirror = q == Q - 1 && g.xh < N;
 #pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = live ? W[q * P + off + l + LQ * j] : float2{0.f, 0.f};
+  for (int j = 0; j < E; ++j) {
+    const int k = l + LQ * j;
+    float2 z = float2{0.f, 0.f};
+    if (live) {
+      if (mirror && 2 * k > N) {
+        z = W[q * P + off + (N - k)];
+        z.y = -z.y;
+      } else {
+        z = W[q * P + off + k];
+      }
+    }
+    v[j] = z;
+  }
   F::inv(v, buf, tw, l);
 
   if (MODE == ROW_INV_OUT) {
@@ -166,7 +185,8 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   F::fwd(v, buf, tw, l);
   if (live) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) W[q * P + off + l + LQ * j] = v[j];
+    for (int j = 0; j < E; ++j)
+      if (q < Q - 1 || l + LQ * j < g.xh) W[q * P + off + l + LQ * j] = v[j];
   }
   if (!sp.do_stats) return;
   finalize_step_stats(sp, ps, redd, redi, &s_flag);
@@ -177,7 +197,7 @@ __host__ __device__ constexpr int wcol_lq(int L) { return L == 1024 ? 32 : 16; }
 // Strided-axis pass (y in 2-D; y and z in 3-D) on a tile of TX adjacent
 // x-columns of one complex plane.
 template <int MODE, int L, int TX>
-__global__ void __launch_bounds__(TX * wcol_lq(L))
+__global__ void __launch_bounds__(TX * wcol_lq(L), wcol_minb(L, TX))
 k_wcol(Geom g, Tables<float> t, float2* W, StatsPtrs sp, int axis) {
   constexpr int LQ = wcol_lq(L);
   using F = WarpFFT<L, LQ>;
@@ -190,14 +210,10 @@ k_wcol(Geom g, Tables<float> t, float2* W, StatsPtrs sp, int axis) {
 
   float2* tile = reinterpret_cast<float2*>(smem_raw);
   const long long es = (axis == 1) ? (long long)g.nx : (long long)g.nx * g.ny;
-  const int xt = g.nx / TX;
   const int nouter = (axis == 1) ? g.nz : g.ny;
   const long long ostride = (axis == 1) ? (long long)g.nx * g.ny : (long long)g.nx;
-  const int per_plane = nouter * xt;
-  const int q = blockIdx.x / per_plane;
-  const int rem = blockIdx.x - q * per_plane;
-  const int o = rem / xt;
-  const int x0 = (rem - o * xt) * TX;
+  int q, o, x0;
+  col_tile(g, nouter, TX, blockIdx.x, q, o, x0);
   float2* base = W + (long long)q * g.P + (long long)o * ostride + x0;
   const int tid = threadIdx.x;
   const int c = tid / LQ, l = tid - c * LQ;
@@ -231,12 +247,13 @@ k_wcol(Geom g, Tables<float> t, float2* W, StatsPtrs sp, int axis) {
     const float omx = t.om[0][x];
     const float fo = gxx * go * t.inv_p;
     const float omo2 = gxx * go;
+    const float wx = col_weight(g, q, x);
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int p = l + LQ * j;
       const float omv = omx + gxx * omo + omo2 * __ldg(&omL[p]);  // 1 - g without cancellation
       const float2 z = v[j];
-      acc += omv * (z.x * z.x + z.y * z.y);
+      acc += wx * omv * (z.x * z.x + z.y * z.y);
       if (MODE == AXIS_FGI) {
         const float f = fo * __ldg(&gL[p]);
         v[j] = float2{z.x * f, z.y * f};
@@ -317,7 +334,7 @@ cudaError_t wcol_m(const Geom& g, const Tables<float>& t, void* W, const StatsPt
   cudaError_t e = set_smem_once(k, smem, done);
   if (e != cudaSuccess || prepare_only) return e;
   const int nouter = axis == 1 ? g.nz : g.ny;
-  const int tiles = g.Q * nouter * (g.nx / TX);
+  const int tiles = col_tiles(g, nouter, TX);
   k<<<tiles, TX * wcol_lq(L), smem, s>>>(g, t, static_cast<float2*>(W), sp, axis);
   return cudaGetLastError();
 }

@@ -477,6 +477,9 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   g.C = n * n;
   g.Q = (g.C + 1) / 2;
   g.tau = tau;
+  g.xh = g.nx;
+  if ((g.C & 1) && dtype == MBO_F32 && axis_plan(g, 0, true).lq)
+    g.xh = std::min(g.nx, ((g.nx / 2 + 1 + 15) / 16) * 16);
   cudaGetDevice(&h->dev);
   // launch shapes
   h->tx = pick_tx(g.nx, dtype == MBO_F32 ? 8 : 4);

@@ -77,7 +77,45 @@ struct Geom {
   long long P;
   int n, C, Q;
   double tau;
+  // x-columns of the last complex plane that the workspace keeps and the
+  // strided passes transform.  nx, unless that plane carries one real
+  // channel (n*n odd) and the x spectrum is in natural order: its spectrum is
+  // then Hermitian along x, columns kx > nx/2 are the conjugates of columns
+  // nx - kx, and only the first xh = min(nx, roundup(nx/2 + 1, 16)) are kept.
+  int xh;
 };
+
+// Tile count of a strided pass (tiles of tx x-columns, nouter outer rows per plane).
+__host__ __device__ inline int col_tiles(const Geom& g, int nouter, int tx) {
+  return (g.Q - 1) * nouter * (g.nx / tx) + nouter * (g.xh / tx);
+}
+// Plane q, outer index o and first column x0 of strided-pass tile b.
+__host__ __device__ inline void col_tile(const Geom& g, int nouter, int tx, int b, int& q, int& o,
+                                         int& x0) {
+  const int xt = g.nx / tx;
+  const int full = (g.Q - 1) * nouter * xt;
+  if (b < full) {
+    q = b / (nouter * xt);
+    const int rem = b - q * nouter * xt;
+    o = rem / xt;
+    x0 = (rem - o * xt) * tx;
+  } else {
+    const int xtl = g.xh / tx;
+    const int rem = b - full;
+    q = g.Q - 1;
+    o = rem / xtl;
+    x0 = (rem - o * xtl) * tx;
+  }
+}
+// Weight of spectrum column kx of plane q in the Parseval sums: 2 for the
+// kept half of a Hermitian plane (each column stands for itself and its
+// conjugate), 1 for its self-conjugate columns 0 and nx/2 and for full
+// planes, 0 for the padding columns past nx/2.
+__host__ __device__ inline float col_weight(const Geom& g, int q, int kx) {
+  if (q != g.Q - 1 || g.xh == g.nx) return 1.f;
+  if (kx == 0 || 2 * kx == g.nx) return 1.f;
+  return 2 * kx < g.nx ? 2.f : 0.f;
+}
 
 // Per-axis tables in the element type R (0 = x, 1 = y, 2 = z).
 template <typename R> struct Tables {

@@ -33,6 +33,36 @@ template <typename R> struct PointStats {
   int fallback = 0;
 };
 
+// Out-of-line forms of the rarely taken projections (quaternion form, FP64
+// re-projection): their code stays out of the hot loop's instruction stream.
+// Matrices pass by value so that the callers' arrays stay in registers.
+template <int NM> struct MatV { float v[NM * NM]; };
+template <int NM> struct ProjV {
+  float b[NM * NM];
+  float sg;
+  float gap;
+};
+
+template <int NM> __device__ __noinline__ ProjV<NM> quat_cold(MatV<NM> m, float sg) {
+  ProjV<NM> r;
+  r.sg = sg;
+  r.gap = polar3_quat(m.v, sg, r.b);
+  return r;
+}
+
+template <int NM> __device__ __noinline__ ProjV<NM> f64_cold(MatV<NM> m) {
+  constexpr int C = NM * NM;
+  double md[C], bd[C], sd;
+#pragma unroll
+  for (int c = 0; c < C; ++c) md[c] = (double)m.v[c];
+  ProjV<NM> r;
+  r.sg = (float)polar_f64<NM>(md, bd, sd);
+#pragma unroll
+  for (int c = 0; c < C; ++c) r.b[c] = (float)bd[c];
+  r.gap = 0.f;
+  return r;
+}
+
 // The quaternion projection's accuracy bound (s2 + s3) / |m|_F >= kQuatGap
 // keeps its error (about 4e-7 / ((s2 + s3) / s1) in FP32) well inside the
 // FP32 step tolerance.
@@ -59,7 +89,13 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
     const float lim = fmaxf(fb, 1e-6f * sqrtf(nx));
     sg = polar3_newton<10, 2>(m, b, est, lim);
     if (est > lim) return true;
-    return polar3_quat(m, sg, b) >= kQuatGap;
+    MatV<3> mv;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) mv.v[k] = m[k];
+    const ProjV<3> r = quat_cold<3>(mv, sg);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b[k] = r.b[k];
+    return r.gap >= kQuatGap;
   } else {
     float sm;
     sg = polar<NM>(m, b, sm);
@@ -71,13 +107,18 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
 template <int NM, typename R>
 __device__ __forceinline__ R project_point_f64(const R* m, R* b) {
   constexpr int C = NM * NM;
-  double md[C], bd[C], sd;
+  if constexpr (sizeof(R) == 4) {
+    MatV<NM> mv;
 #pragma unroll
-  for (int c = 0; c < C; ++c) md[c] = (double)m[c];
-  const double sg = polar_f64<NM>(md, bd, sd);
+    for (int c = 0; c < C; ++c) mv.v[c] = m[c];
+    const ProjV<NM> r = f64_cold<NM>(mv);
 #pragma unroll
-  for (int c = 0; c < C; ++c) b[c] = (R)bd[c];
-  return (R)sg;
+    for (int c = 0; c < C; ++c) b[c] = r.b[c];
+    return r.sg;
+  } else {
+    double sd;
+    return polar_f64<NM>(m, b, sd);
+  }
 }
 
 // Record a projected point: compare with the old field, write the new value
@@ -290,15 +331,10 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   const int tx = 1 << ltx;
   const int L = (axis == 1) ? g.ny : g.nz;
   const long long es = (axis == 1) ? (long long)g.nx : (long long)g.nx * g.ny;
-  const int xt = g.nx >> ltx;
   const int nouter = (axis == 1) ? g.nz : g.ny;
   const long long ostride = (axis == 1) ? (long long)g.nx * g.ny : (long long)g.nx;
-  const int per_plane = nouter * xt;
-  const int tile = blockIdx.x;
-  const int q = tile / per_plane;
-  const int rem = tile - q * per_plane;
-  const int o = rem / xt;
-  const int x0 = (rem - o * xt) << ltx;
+  int q, o, x0;
+  col_tile(g, nouter, 1 << ltx, blockIdx.x, q, o, x0);
   V* base = W + (long long)q * g.P + (long long)o * ostride + x0;
   const ColLayout lay{ltx};
   const int T = blockDim.x, tid = threadIdx.x;
@@ -332,11 +368,12 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
     const R omx = t.om[0][x];
     const R fo = gxx * go * t.inv_p;
     const R omo2 = gxx * go;
+    const R wx = (R)col_weight(g, q, x);
     for (int p = p0; p < L; p += dp) {
       const int e = lay.addr(mcol, p);
       const R omv = omx + gxx * omo + omo2 * omL[p];  // 1 - g without cancellation
       V z = s[e];
-      acc += omv * (z.x * z.x + z.y * z.y);
+      acc += wx * omv * (z.x * z.x + z.y * z.y);
       if (MODE == AXIS_FGI) {
         const R f = fo * gL[p];
         s[e] = V{z.x * f, z.y * f};
@@ -592,7 +629,7 @@ static cudaError_t launch_axis_m(const Geom& g, const Tables<R>& t, void* W, con
   int ltx = 0;
   while ((1 << ltx) < tx) ++ltx;
   const int nouter = axis == 1 ? g.nz : g.ny;
-  const int tiles = g.Q * nouter * (g.nx / tx);
+  const int tiles = col_tiles(g, nouter, tx);
   k<<<tiles, threads, smem, s>>>(g, t, static_cast<typename VT<R>::V*>(W), sp, axis, ltx);
   return cudaGetLastError();
 }

@@ -169,6 +169,7 @@ extern "C" mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, 
   g.C = n * n;
   g.Q = (g.C + 1) / 2;
   g.tau = tau;
+  g.xh = g.nx;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == MBO_F32) return diffuse_noalloc<float>(g, A, A_tilde, s);
   return diffuse_noalloc<double>(g, A, A_tilde, s);

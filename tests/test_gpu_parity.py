@@ -360,3 +360,44 @@ def test_max_size_rows_and_columns(M):
         torch.cuda.synchronize()
         assert np.abs(host(out) - O.diffuse(A, tau)).max() < (F64_TOL if dtype == "f64" else F32_DIFF_TOL)
         h.close()
+
+
+def test_project_small_sigma_min_f32_routes(M):
+    """FP32 n = 3 points with a small smallest singular value: the quaternion
+    form (sigma_2 + sigma_3 away from 0) and the FP64 re-projection (both
+    small) must both meet the FP32 bound against the oracle's FP64 polar
+    factor of Lemma 1.1, in both determinant classes."""
+    g = I.rng(4242)
+    configs = [(1.0, 0.9, 1e-7), (1.0, 0.5, 1e-5), (5.0, 2.0, 1e-3), (5.0, 0.5, 2e-4),
+               (1.0, 0.2, 5e-4), (5.0, 0.2, 0.05), (3.0, 0.05, 0.02), (1.0, 1.0, 1e-6)]
+    mats_ = []
+    for s in configs:
+        for _ in range(64):
+            U = np.linalg.qr(g.standard_normal((3, 3)))[0]
+            V = np.linalg.qr(g.standard_normal((3, 3)))[0]
+            Mx = U @ np.diag(s) @ V.T
+            mats_.append(Mx)
+            mats_.append(-Mx)
+    Ms = np.stack(mats_)                                   # (1024, 3, 3)
+    At = Ms.reshape(32, 32, 9).transpose(2, 0, 1).copy()   # (9, 32, 32)
+    dims = At.shape[1:]
+    ref, sref = O.project(At, 3, return_sign=True)
+    h = M.Mbo(dims, 3, 1e-3, "f32")
+    a = dev(At, torch.float32)
+    out = torch.empty_like(a)
+    sg = torch.empty(dims, dtype=torch.int8, device="cuda")
+    h.project(a, out, sg)
+    torch.cuda.synchronize()
+    B = host(out)
+    Bm = mats(B, 3)
+    assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(3)).max() < 2e-6
+    d = np.abs(dets(At, 3)).reshape(dims)
+    unamb = d > 1e-4
+    assert unamb.sum() >= 448
+    assert np.array_equal(sg.cpu().numpy()[unamb], sref[unamb])
+    cs = cond_sum(At, 3).reshape(dims)
+    eps_in = np.abs(At - At.astype(np.float32).astype(np.float64)).max(axis=0)
+    bound = F32_STEP_TOL + 2 * (eps_in * 3 + 1e-7) / np.maximum(cs, 1e-30)
+    err = np.abs(B - ref).max(axis=0)
+    assert np.all(err[unamb] <= bound[unamb])
+    h.close()
