@@ -62,9 +62,16 @@ typedef enum {
 
 /* Options; mbo_default_config fills the defaults. */
 typedef struct {
-  double fallback_sigma; /* MBO_F32: points whose smallest singular value of A~
-                            is below this are re-projected in FP64 from the FP32
-                            A~ (default 1e-3; <= 0 disables).  Ignored for F64. */
+  double fallback_sigma; /* MBO_F32.  n = 3: points whose smallest-singular-value
+                            estimate |det A~| / |cof A~|_F is at most
+                            max(fallback_sigma, 1e-6 |A~|_F) skip the FP32
+                            Newton iteration and take an exact form instead:
+                            the quaternion form where (s2 + s3) / |A~|_F is
+                            not small, else FP64 re-projection from the FP32
+                            A~.  n = 2: points whose smallest singular value is
+                            below it are re-projected in FP64.  Default 0: only
+                            points singular to single precision.  Ignored for
+                            F64.                                                   */
   int check_interval;    /* run loop: the host reads the step records every this
                             many steps to test for stationarity (default 16).    */
   int use_graph;         /* run loop: replay the step from a captured CUDA graph

@@ -411,7 +411,7 @@ const char* mbo_last_error(mbo_handle h) { return h ? h->err : ""; }
 
 void mbo_default_config(mbo_config* cfg) {
   if (!cfg) return;
-  cfg->fallback_sigma = 1e-3;
+  cfg->fallback_sigma = 0.0;
   cfg->check_interval = 16;
   cfg->use_graph = 1;
   cfg->row_threads = 0;

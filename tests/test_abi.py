@@ -68,5 +68,5 @@ def test_null_handle_rejected(lib):
 
 def test_default_config(lib):
     c = M.mbo_default_config()
-    assert c.fallback_sigma == pytest.approx(1e-3)
+    assert c.fallback_sigma == 0.0
     assert c.check_interval == 16 and c.use_graph == 1
