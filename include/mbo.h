@@ -28,7 +28,7 @@
  *     problems (non-finite values, a wait that gave up) are recorded in the
  *     handle and reported by the next call that synchronises.
  *   - A handle is not thread safe; distinct handles are independent.
- *   - Supported sizes: every N_j = 2^a 3^b with 2 <= N_j <= 2048; n in {1,2,3};
+ *   - Supported sizes: every N_j = 2^a 3^b with 2 <= N_j <= 2048; n in {1,2,3,4};
  *     other sizes return MBO_ERR_UNSUPPORTED_SIZE.
  */
 #ifndef MBO_GB300_H
@@ -62,16 +62,16 @@ typedef enum {
 
 /* Options; mbo_default_config fills the defaults. */
 typedef struct {
-  double fallback_sigma; /* MBO_F32.  n = 3: points whose smallest-singular-value
-                            estimate |det A~| / |cof A~|_F is at most
-                            max(fallback_sigma, 1e-6 |A~|_F) skip the FP32
-                            Newton iteration and take an exact form instead:
-                            the quaternion form where (s2 + s3) / |A~|_F is
-                            not small, else FP64 re-projection from the FP32
-                            A~.  n = 2: points whose smallest singular value is
-                            below it are re-projected in FP64.  Default 0: only
-                            points singular to single precision.  Ignored for
-                            F64.                                                   */
+  double fallback_sigma; /* MBO_F32.  n = 3 and 4: points whose smallest-
+                            singular-value estimate |det A~| / |cof A~|_F is at
+                            most max(fallback_sigma, 1e-6 |A~|_F), or that are
+                            singular to single precision, skip the FP32 Newton
+                            iteration and take an exact form instead: for n = 3
+                            the quaternion form where (s2 + s3) / |A~|_F is not
+                            small, else (and always for n = 4) FP64
+                            re-projection from the FP32 A~.  n = 2: points whose
+                            smallest singular value is below it are re-projected
+                            in FP64.  Default 0.  Ignored for F64.                 */
   int check_interval;    /* run loop: the host reads the step records every this
                             many steps to test for stationarity (default 16).    */
   int use_graph;         /* run loop: replay the step from a captured CUDA graph
@@ -98,7 +98,7 @@ MBO_API void mbo_default_config(mbo_config* cfg);
 /* Create a handle for one field geometry.
  *   out   receives the handle (set to NULL on failure).
  *   ndim  2 or 3; dims[ndim] as in the conventions above.
- *   n     matrix order (1, 2 or 3); tau > 0 the diffusion time of one step.
+ *   n     matrix order (1 to 4); tau > 0 the diffusion time of one step.
  *   cfg   NULL for the defaults.
  * Allocates the spectral workspace (ceil(n*n/2) complex planes of P points)
  * and small tables on the current device.  Synchronous. */
@@ -219,7 +219,8 @@ MBO_API mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, dou
  * lie in SO(n) after the step (0 <= n_plus <= P); < 0 keeps the number of
  * points of A with det > 0.  stats as in mbo_step (energy of the input).
  * Allocates the step's buffers (a field copy and 8 bytes per point) on first
- * use. */
+ * use.  Handles of order n = 4 return MBO_ERR_UNSUPPORTED_SIZE (both volume
+ * calls). */
 MBO_API mbo_status mbo_step_volume(mbo_handle h, void* A, int64_t n_plus, mbo_stats* stats,
                                    void* stream);
 

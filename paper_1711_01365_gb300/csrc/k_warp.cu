@@ -22,12 +22,13 @@ namespace {
 __host__ __device__ constexpr int wrow_lq(int N) { return N == 1024 ? 32 : 16; }
 __host__ __device__ constexpr int wrow_rb(int N) { return N == 1024 ? 1 : 2; }  // rows per block: whole warps
 
-// Blocks per SM the register budget is sized for.
-__host__ __device__ constexpr int wrow_minb(int N) { return N > 0 ? 4 : 4; }
+// Blocks per SM the register budget is sized for (n <= 3: 160-thread blocks
+// at 96 registers; n = 4: 256-thread blocks at 128).
+__host__ __device__ constexpr int wrow_minb(int N, int NM) { return N > 0 && NM <= 3 ? 4 : 2; }
 __host__ __device__ constexpr int wcol_minb(int L, int TX) { return L > 0 && TX == 8 ? 2 : 3; }
 
 template <int NM, int MODE, int N>
-__global__ void __launch_bounds__(wrow_rb(N) * ((NM * NM + 1) / 2) * wrow_lq(N), wrow_minb(N))
+__global__ void __launch_bounds__(wrow_rb(N) * ((NM * NM + 1) / 2) * wrow_lq(N), wrow_minb(N, NM))
 k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2* W, StatsPtrs sp,
        float fb_sigma) {
   constexpr int LQ = wrow_lq(N), RB = wrow_rb(N);
@@ -321,6 +322,7 @@ cudaError_t wrow_n(RowMode mode, const Geom& g, const Tables<float>& t, const fl
   MBO_WROW_CASE(1)
   MBO_WROW_CASE(2)
   MBO_WROW_CASE(3)
+  MBO_WROW_CASE(4)
 #undef MBO_WROW_CASE
   return cudaErrorInvalidValue;
 }

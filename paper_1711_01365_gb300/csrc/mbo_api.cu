@@ -452,7 +452,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
                       mbo_dtype dtype, const mbo_config* cfg) {
   if (!out) return MBO_ERR_INVALID_ARG;
   *out = nullptr;
-  if ((ndim != 2 && ndim != 3) || !dims || n < 1 || n > 3 || !(tau > 0) || !std::isfinite(tau) ||
+  if ((ndim != 2 && ndim != 3) || !dims || n < 1 || n > 4 || !(tau > 0) || !std::isfinite(tau) ||
       (dtype != MBO_F32 && dtype != MBO_F64))
     return MBO_ERR_INVALID_ARG;
   for (int i = 0; i < ndim; ++i) {
@@ -882,6 +882,7 @@ static mbo_status vp_step(mbo_handle h, void* A, long long n_plus, bool respect_
 
 mbo_status mbo_step_volume(mbo_handle h, void* A, int64_t n_plus, mbo_stats* stats, void* stream) {
   if (!h) return MBO_ERR_INVALID_ARG;
+  if (h->g.n > 3) return fail(h, MBO_ERR_UNSUPPORTED_SIZE, "the volume-preserving step supports n <= 3");
   mbo_status rc;
   if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
   if (n_plus > h->g.P) return fail(h, MBO_ERR_INVALID_ARG, "n_plus exceeds the number of points");
@@ -902,6 +903,7 @@ mbo_status mbo_step_volume(mbo_handle h, void* A, int64_t n_plus, mbo_stats* sta
 mbo_status mbo_run_volume(mbo_handle h, void* A, int64_t n_plus, int max_steps, double tol,
                           int* steps_taken, int* stationary, double* energies, void* stream) {
   if (!h || max_steps < 0) return MBO_ERR_INVALID_ARG;
+  if (h->g.n > 3) return fail(h, MBO_ERR_UNSUPPORTED_SIZE, "the volume-preserving step supports n <= 3");
   mbo_status rc;
   if ((rc = check_field_ptr(h, A, "A")) != MBO_OK) return rc;
   if (n_plus > h->g.P) return fail(h, MBO_ERR_INVALID_ARG, "n_plus exceeds the number of points");

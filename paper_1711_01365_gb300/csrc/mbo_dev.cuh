@@ -540,67 +540,138 @@ template <typename R> __device__ __forceinline__ R cofactor3(const R* X, R* C) {
   return X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
 }
 
-// n = 3, scaled Newton iteration for the polar factor (Higham 1986):
+// Determinant of a 4x4 matrix (row-major) by complementary 2x2 minors.
+template <typename R> __device__ __forceinline__ R det4(const R* X) {
+  const R t01 = X[0] * X[5] - X[1] * X[4], t02 = X[0] * X[6] - X[2] * X[4];
+  const R t03 = X[0] * X[7] - X[3] * X[4], t12 = X[1] * X[6] - X[2] * X[5];
+  const R t13 = X[1] * X[7] - X[3] * X[5], t23 = X[2] * X[7] - X[3] * X[6];
+  const R b01 = X[8] * X[13] - X[9] * X[12], b02 = X[8] * X[14] - X[10] * X[12];
+  const R b03 = X[8] * X[15] - X[11] * X[12], b12 = X[9] * X[14] - X[10] * X[13];
+  const R b13 = X[9] * X[15] - X[11] * X[13], b23 = X[10] * X[15] - X[11] * X[14];
+  return t01 * b23 - t02 * b13 + t03 * b12 + t12 * b03 - t13 * b02 + t23 * b01;
+}
+
+// n = 4: cofactor matrix C[i*4+j] = (-1)^(i+j) M_ij of X (row-major) from the
+// 2x2 minors of rows (0, 1) and rows (2, 3): each 3x3 minor is expanded along
+// the row that the deleted one leaves alone in its pair.  Returns det X.
+template <typename R> __device__ __forceinline__ R cofactor4(const R* X, R* C) {
+  const R t01 = X[0] * X[5] - X[1] * X[4], t02 = X[0] * X[6] - X[2] * X[4];
+  const R t03 = X[0] * X[7] - X[3] * X[4], t12 = X[1] * X[6] - X[2] * X[5];
+  const R t13 = X[1] * X[7] - X[3] * X[5], t23 = X[2] * X[7] - X[3] * X[6];
+  const R b01 = X[8] * X[13] - X[9] * X[12], b02 = X[8] * X[14] - X[10] * X[12];
+  const R b03 = X[8] * X[15] - X[11] * X[12], b12 = X[9] * X[14] - X[10] * X[13];
+  const R b13 = X[9] * X[15] - X[11] * X[13], b23 = X[10] * X[15] - X[11] * X[14];
+  C[0] = X[5] * b23 - X[6] * b13 + X[7] * b12;
+  C[1] = -(X[4] * b23 - X[6] * b03 + X[7] * b02);
+  C[2] = X[4] * b13 - X[5] * b03 + X[7] * b01;
+  C[3] = -(X[4] * b12 - X[5] * b02 + X[6] * b01);
+  C[4] = -(X[1] * b23 - X[2] * b13 + X[3] * b12);
+  C[5] = X[0] * b23 - X[2] * b03 + X[3] * b02;
+  C[6] = -(X[0] * b13 - X[1] * b03 + X[3] * b01);
+  C[7] = X[0] * b12 - X[1] * b02 + X[2] * b01;
+  C[8] = X[13] * t23 - X[14] * t13 + X[15] * t12;
+  C[9] = -(X[12] * t23 - X[14] * t03 + X[15] * t02);
+  C[10] = X[12] * t13 - X[13] * t03 + X[15] * t01;
+  C[11] = -(X[12] * t12 - X[13] * t02 + X[14] * t01);
+  C[12] = -(X[9] * t23 - X[10] * t13 + X[11] * t12);
+  C[13] = X[8] * t23 - X[10] * t03 + X[11] * t02;
+  C[14] = -(X[8] * t13 - X[9] * t03 + X[11] * t01);
+  C[15] = X[8] * t12 - X[9] * t02 + X[10] * t01;
+  return X[0] * C[0] + X[1] * C[1] + X[2] * C[2] + X[3] * C[3];
+}
+
+template <int NM, typename R> __device__ __forceinline__ R cofactor_n(const R* X, R* C) {
+  if constexpr (NM == 3) return cofactor3(X, C);
+  else return cofactor4(X, C);
+}
+
+// n = 3 and 4, scaled Newton iteration for the polar factor (Higham 1986):
 //   X <- (zeta X + X^{-t} / zeta) / 2,  zeta = (|X^{-1}|_F / |X|_F)^{1/2},
 // with X^{-t} = cof(X) / det(X).  With X = Q H, cof(X) = det(X) Q H^{-1}, so
 // a X + c cof(X) = Q (a H + c det(X) H^{-1}) keeps the polar factor Q for any
 // a > 0 and c det(X) > 0: the scaled phase only sets the speed, and its
-// coefficients are computed in FP32 whatever R is.  The scaled phase ends
-// when |X|_F^2 = sum s_i^2 is within 1e-4 of 3 and zeta within 1e-5 of 1:
-// then sum s_i^2 * sum s_i^-2 is within ~1e-4 of 9, its minimum, which by the
+// coefficients are computed in FP32 whatever R is (callers keep det m^2 in
+// the FP32 range).  The scaled phase ends when
+// |X|_F^2 = sum s_i^2 is within 1e-4 of n and zeta within 1e-5 of 1: then
+// sum s_i^2 * sum s_i^-2 is within ~1e-4 of n^2, its minimum, which by the
 // AM-HM inequality holds only when every s_i^2 is close to 1 (zeta = 1 alone
 // does not suffice: s = (2, 1/2, 1) gives zeta = 1).  NUN unscaled iterations
 // X <- (X + X^{-t}) / 2 follow; each squares the distance to orthogonality
 // (d -> d^2 / 2) and their fixed point is exactly orthogonal.  det X keeps
-// the sign of det m.  est receives |det m| / |cof m|_F, which lies in
-// [sigma_min / sqrt(3), sigma_min]; points with est <= skip_below (exactly
-// singular ones, where the iteration is undefined, included) are returned
-// unprocessed for the caller to route elsewhere.
-template <int ITMAX, int NUN, typename R>
-__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R skip_below = R(0)) {
-  R X[9], C[9];
+// the sign of det m, and the returned class is the sign of det of the last
+// iterate (the two differ only where det m is below its rounding error).
+// est receives |det m| / |cof m|_F = 1 / |m^{-1}|_F, which lies in
+// [sigma_min / sqrt(n), sigma_min], or 0 where |cof m|_F^2 <= cof2_floor
+// (callers pass (c |m|_F^(n-1))^2 with c above the rounding error of cof:
+// below it the matrix has rank <= n - 2 to working precision, est is noise
+// over noise and the iteration would run on noise).  Points with
+// est <= skip_below (exactly singular ones, where the iteration is undefined,
+// included) are returned unprocessed, with the sign of det m, for the caller
+// to route elsewhere, and est is set to 0 where the iteration overflowed.
+template <int NM, int ITMAX, int NUN, typename R>
+__device__ __forceinline__ R polar_newton(const R* m, R* b, R& est, R skip_below = R(0),
+                                          R cof2_floor = R(0)) {
+  constexpr int C2 = NM * NM;
+  R X[C2], C[C2];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) X[k] = m[k];
-  R det = cofactor3(X, C);
+  for (int k = 0; k < C2; ++k) X[k] = m[k];
+  R det = cofactor_n<NM>(X, C);
   const R sg = (det >= R(0)) ? R(1) : R(-1);
   {
     R nc = R(0);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
+    for (int k = 0; k < C2; ++k) nc += C[k] * C[k];
     est = fabs(det) * rsqrt_(nc);
+    // at rank <= n - 2 (to working precision) cof m is rounding noise and est
+    // noise over noise: callers pass a floor for |cof m|_F^2
+    if (!(nc > cof2_floor)) est = R(0);
   }
   if (!(est > skip_below)) {  // singular, not finite or below the caller's limit: caller's fallback
 #pragma unroll
-    for (int k = 0; k < 9; ++k) b[k] = X[k];
+    for (int k = 0; k < C2; ++k) b[k] = X[k];
     return sg;
   }
 #pragma unroll 1
   for (int it = 0; it < ITMAX; ++it) {
     float nx = 0.f, nc = 0.f;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < C2; ++k) {
       nx += (float)X[k] * (float)X[k];
       nc += (float)C[k] * (float)C[k];
     }
     const float fd = (float)det;
     const float zf = rsqrtf(rsqrtf(__fdividef(nc, fd * fd * nx)));  // (nc / (det^2 nx))^{1/4}
-    if (fabsf(zf - 1.0f) < 1e-5f && fabsf(nx - 3.0f) < 1e-4f) break;
+    if (fabsf(zf - 1.0f) < 1e-5f && fabsf(nx - (float)NM) < 1e-4f) break;
     const R a = R(0.5f * zf);
     const R c = R(__fdividef(0.5f, zf * fd));
 #pragma unroll
-    for (int k = 0; k < 9; ++k) X[k] = a * X[k] + c * C[k];
-    det = cofactor3(X, C);
+    for (int k = 0; k < C2; ++k) X[k] = a * X[k] + c * C[k];
+    det = cofactor_n<NM>(X, C);
   }
+  R c = R(0);
 #pragma unroll
   for (int it = 0; it < NUN; ++it) {
-    const R c = R(0.5) * recip(det);
+    c = R(0.5) * recip(det);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) X[k] = R(0.5) * X[k] + c * C[k];
-    if (it + 1 < NUN) det = cofactor3(X, C);
+    for (int k = 0; k < C2; ++k) X[k] = R(0.5) * X[k] + c * C[k];
+    if (it + 1 < NUN) det = cofactor_n<NM>(X, C);
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) b[k] = X[k];
-  return sg;
+  for (int k = 0; k < C2; ++k) b[k] = X[k];
+  // At rank <= n - 2 (to working precision) the iteration runs on rounding
+  // noise and can overflow: report it as singular (est = 0) for the caller's
+  // fallback.
+  if (!(fabs(c) < R(1e30)) || !(fabs(X[0]) < R(1e30))) est = R(0);
+  // The class of the limit: det keeps its sign along the iteration, but where
+  // det m is below its own rounding error its computed sign is noise and the
+  // iterates settle the class; report the one b has.
+  return det >= R(0) ? R(1) : R(-1);
+}
+
+template <int ITMAX, int NUN, typename R>
+__device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R skip_below = R(0),
+                                           R cof2_floor = R(0)) {
+  return polar_newton<3, ITMAX, NUN>(m, b, est, skip_below, cof2_floor);
 }
 
 // n = 3, FP32: the nearest matrix of the class sg (det = sg) through the
@@ -706,16 +777,153 @@ template <int NM, typename R> __device__ __forceinline__ R polar(const R* m, R* 
   else return polar3(m, b, smin);
 }
 
+// n = 4, FP64, for matrices singular to working precision: one-sided
+// (Hestenes) Jacobi on the columns of m gives m V = [a_0 .. a_3] with
+// orthogonal columns; U = a_j / |a_j|, columns of negligible norm completed by
+// Gram-Schmidt of the basis vector that leaves the largest remainder; the
+// column of the smallest singular value is flipped when needed so that
+// det(U V^t) = sign det m (Lemma 1.1, det m = 0 -> +1).  b = U V^t.
+static __device__ __noinline__ double polar4_jacobi(const double* m, double* b, double& smin) {
+  double a[4][4], v[4][4];  // a[j] = column j of m V, v[j] = column j of V
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[j][i] = m[i * 4 + j];
+      v[j][i] = (i == j) ? 1.0 : 0.0;
+    }
+  auto dot4 = [](const double* x, const double* y) {
+    return x[0] * y[0] + x[1] * y[1] + x[2] * y[2] + x[3] * y[3];
+  };
+#pragma unroll 1
+  for (int sw = 0; sw < 16; ++sw) {
+    bool rot = false;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = p + 1; q < 4; ++q) {
+        const double al = dot4(a[p], a[p]), be = dot4(a[q], a[q]), ga = dot4(a[p], a[q]);
+        if (fabs(ga) > 2e-15 * sqrt(al * be)) {
+          const double ze = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, ze) / (fabs(ze) + sqrt(1.0 + ze * ze));
+          const double c = rsqrt(1.0 + t * t), s = c * t;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double ap = a[p][i], aq = a[q][i];
+            a[p][i] = c * ap - s * aq;
+            a[q][i] = s * ap + c * aq;
+            const double vp = v[p][i], vq = v[q][i];
+            v[p][i] = c * vp - s * vq;
+            v[q][i] = s * vp + c * vq;
+          }
+          rot = true;
+        }
+      }
+    if (!rot) break;
+  }
+  double sgm[4], U[4][4];
+  bool have[4];
+  double nmax = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    sgm[j] = sqrt(dot4(a[j], a[j]));
+    nmax = fmax(nmax, sgm[j]);
+  }
+  int is = 0;
+#pragma unroll
+  for (int j = 1; j < 4; ++j)
+    if (sgm[j] < sgm[is]) is = j;
+  smin = sgm[is];
+  const double want = det4(m) >= 0.0 ? 1.0 : -1.0;
+  if (!(nmax > 0.0)) {  // m = 0: the identity
+#pragma unroll
+    for (int k = 0; k < 16; ++k) b[k] = (k % 5 == 0) ? 1.0 : 0.0;
+    return 1.0;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    have[j] = sgm[j] > 1e-13 * nmax;
+    const double inv = have[j] ? 1.0 / sgm[j] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) U[j][i] = a[j][i] * inv;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (have[j]) continue;
+    double best[4] = {0.0, 0.0, 0.0, 0.0}, bn = -1.0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double w[4] = {0.0, 0.0, 0.0, 0.0};
+      w[e] = 1.0;
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!have[k]) continue;
+          const double d = dot4(U[k], w);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) w[i] -= d * U[k][i];
+        }
+      const double wn = dot4(w, w);
+      if (wn > bn) {
+        bn = wn;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best[i] = w[i];
+      }
+    }
+    const double inv = rsqrt(bn);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) U[j][i] = best[i] * inv;
+    have[j] = true;
+  }
+  double um[16], vm[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      um[i * 4 + j] = U[j][i];
+      vm[i * 4 + j] = v[j][i];
+    }
+  if ((det4(um) * det4(vm) >= 0.0 ? 1.0 : -1.0) != want) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j == is)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) U[j][i] = -U[j][i];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      b[i * 4 + k] = U[0][i] * v[0][k] + U[1][i] * v[1][k] + U[2][i] * v[2][k] + U[3][i] * v[3][k];
+  return want;
+}
+
 // FP64 projection used by the FP64 path and by the FP32 path's
 // re-projection: Newton, and the one-sided Jacobi construction for matrices
 // that are singular to working precision (rank-deficient ties included).
 template <int NM> __device__ __forceinline__ double polar_f64(const double* m, double* b, double& smin) {
-  if constexpr (NM == 3) {
+  if constexpr (NM == 4) {
+    double nx = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) nx += m[k] * m[k];
+    // Newton only where det m stands clear of its rounding error and its
+    // square of the FP32 range of the scaling coefficients; with two small
+    // singular values est alone does not ensure either
+    const double d = det4(m);
+    if (nx > 1e-30 && nx < 1e30 && d * d > 1e-26 * nx * nx * nx * nx && fabs(d) > 1e-18) {
+      double est = 0.0;
+      const double sg = polar_newton<4, 16, 3>(m, b, est, 1e-12 * sqrt(nx), 1e-24 * nx * nx * nx);
+      smin = est;
+      if (est > 1e-12 * sqrt(nx)) return sg;
+    }
+    return polar4_jacobi(m, b, smin);
+  } else if constexpr (NM == 3) {
     double nx = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
     double est = 0.0;
-    const double sg = polar3_newton<16, 3>(m, b, est, 1e-12 * sqrt(nx));
+    const double sg = polar3_newton<16, 3>(m, b, est, 1e-12 * sqrt(nx), 1e-24 * nx * nx);
     smin = est;
     if (est > 1e-12 * sqrt(nx)) return sg;
     return polar3(m, b, smin);
@@ -729,9 +937,11 @@ template <int NM, typename R> __device__ __forceinline__ R det_sign(const R* m) 
   R d;
   if constexpr (NM == 1) d = m[0];
   else if constexpr (NM == 2) d = m[0] * m[3] - m[1] * m[2];
-  else
+  else if constexpr (NM == 3)
     d = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
         m[2] * (m[3] * m[7] - m[4] * m[6]);
+  else
+    d = det4(m);
   return d >= R(0) ? R(1) : R(-1);
 }
 

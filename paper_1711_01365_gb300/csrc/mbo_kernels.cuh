@@ -73,7 +73,8 @@ constexpr float kQuatGap = 0.05f;
 // iteration for points whose smallest singular value is at least fb (the
 // configured threshold) and not small to single precision; below that the
 // quaternion form, whose error grows with 1 / (s2 + s3) instead of 1 / s3;
-// FP64 only where s2 + s3 is small too.  FP32, n = 2: points whose smallest
+// FP64 only where s2 + s3 is small too.  FP32, n = 4: the same Newton
+// iteration, FP64 below the limit.  FP32, n = 2: points whose smallest
 // singular value is below fb.  FP64 elements are always projected here.
 template <int NM, typename R>
 __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
@@ -81,21 +82,27 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
     double sm;
     sg = polar_f64<NM>(m, b, sm);
     return true;
-  } else if constexpr (NM == 3) {
+  } else if constexpr (NM >= 3) {
     float nx = 0.f;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) nx += m[k] * m[k];
+    for (int k = 0; k < NM * NM; ++k) nx += m[k] * m[k];
     float est = 0.f;
     const float lim = fmaxf(fb, 1e-6f * sqrtf(nx));
-    sg = polar3_newton<10, 2>(m, b, est, lim);
+    // |cof m|_F > 1e-5 |m|_F^(n-1): above the FP32 rounding error of cof
+    const float cf = NM == 3 ? nx * nx : nx * nx * nx;
+    sg = polar_newton<NM, 10, 2>(m, b, est, lim, 1e-10f * cf);
     if (est > lim) return true;
-    MatV<3> mv;
+    if constexpr (NM == 3) {
+      MatV<3> mv;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) mv.v[k] = m[k];
-    const ProjV<3> r = quat_cold<3>(mv, sg);
+      for (int k = 0; k < 9; ++k) mv.v[k] = m[k];
+      const ProjV<3> r = quat_cold<3>(mv, sg);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) b[k] = r.b[k];
-    return r.gap >= kQuatGap;
+      for (int k = 0; k < 9; ++k) b[k] = r.b[k];
+      return r.gap >= kQuatGap;
+    } else {
+      return false;
+    }
   } else {
     float sm;
     sg = polar<NM>(m, b, sm);
@@ -612,6 +619,7 @@ cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R*
   MBO_ROW_CASE(1)
   MBO_ROW_CASE(2)
   MBO_ROW_CASE(3)
+  MBO_ROW_CASE(4)
 #undef MBO_ROW_CASE
   return cudaErrorInvalidValue;
 }
@@ -657,7 +665,8 @@ cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
   const R fb = (R)fallback_sigma;
   if (g.n == 1) k_project<R, 1><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
   else if (g.n == 2) k_project<R, 2><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
-  else k_project<R, 3><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
+  else if (g.n == 3) k_project<R, 3><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
+  else k_project<R, 4><<<(int)blocks, threads, 0, s>>>(g.P, At, B, det_sign, fb);
   return cudaGetLastError();
 }
 
@@ -693,6 +702,7 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>
   MBO_PREP_ROW(1)
   MBO_PREP_ROW(2)
   MBO_PREP_ROW(3)
+  MBO_PREP_ROW(4)
 #undef MBO_PREP_ROW
   for (int axis = 1; axis <= (g.ndim == 3 ? 2 : 1) && e == cudaSuccess; ++axis) {
     e = launch_axis_m<R, AXIS_FWD>(g, t, nullptr, sp, axis, tx, 64, 0, true);

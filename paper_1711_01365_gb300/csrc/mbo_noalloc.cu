@@ -150,7 +150,7 @@ using namespace mbo;
 extern "C" mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, double tau,
                                           mbo_dtype dtype, const void* A, void* A_tilde,
                                           void* stream) {
-  if ((ndim != 2 && ndim != 3) || !dims || n < 1 || n > 3 || !(tau > 0) || !std::isfinite(tau) ||
+  if ((ndim != 2 && ndim != 3) || !dims || n < 1 || n > 4 || !(tau > 0) || !std::isfinite(tau) ||
       (dtype != MBO_F32 && dtype != MBO_F64))
     return MBO_ERR_INVALID_ARG;
   if (!A || !A_tilde || reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(A_tilde) % 16)

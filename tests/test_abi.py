@@ -52,7 +52,7 @@ def test_unsupported_sizes_rejected(lib, dims):
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("args", [((16, 16), 0, 1e-3), ((16, 16), 4, 1e-3), ((16, 16), 2, 0.0),
+@pytest.mark.parametrize("args", [((16, 16), 0, 1e-3), ((16, 16), 5, 1e-3), ((16, 16), 2, 0.0),
                                   ((16, 16), 2, -1.0), ((16,), 2, 1e-3), ((4, 4, 4, 4), 2, 1e-3)])
 def test_invalid_arguments_rejected(lib, args):
     with pytest.raises(M.MboError) as ei:

@@ -401,3 +401,37 @@ def test_project_small_sigma_min_f32_routes(M):
     err = np.abs(B - ref).max(axis=0)
     assert np.all(err[unamb] <= bound[unamb])
     h.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [2, 3])
+def test_project_rotated_rank_deficient_on_gpu(M, n, dtype):
+    """Rotated matrices of rank n-1 and (n = 3) rank 1, whose computed det is
+    rounding noise: the projection must return a minimiser of Lemma 1.1 in the
+    class it reports (|B - A|^2 = sum (s_i - 1)^2; at s_n = 0 both classes are
+    equally close, Lemma 7.1)."""
+    g = I.rng(4300 + n)
+    cols = []
+    for r in range(1, n):
+        for _ in range(64):
+            U = np.linalg.qr(g.standard_normal((n, n)))[0]
+            V = np.linalg.qr(g.standard_normal((n, n)))[0]
+            sv = np.zeros(n)
+            sv[:r] = np.sort(g.uniform(0.2, 2.0, r))[::-1]
+            cols.append((U @ np.diag(sv) @ V.T).reshape(-1))
+    F = np.stack(cols, axis=1).reshape(n * n, 2 * (n - 1), 32)
+    dims = F.shape[1:]
+    h = M.Mbo(dims, n, 1e-3, dtype)
+    a = dev(F, tdt(dtype))
+    out = torch.empty_like(a)
+    sg = torch.empty(dims, dtype=torch.int8, device="cuda")
+    h.project(a, out, sg)
+    torch.cuda.synchronize()
+    Bm = mats(host(out), n)
+    Fm = mats(F, n)
+    assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < (1e-12 if dtype == "f64" else 2e-6)
+    assert np.array_equal(np.sign(np.linalg.det(Bm)).reshape(dims), sg.cpu().numpy().astype(float))
+    s = np.linalg.svd(Fm, compute_uv=False)
+    d2 = ((Bm - Fm) ** 2).sum((1, 2))
+    assert np.abs(d2 - ((s - 1) ** 2).sum(1)).max() < (1e-9 if dtype == "f64" else 2e-5)
+    h.close()

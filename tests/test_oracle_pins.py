@@ -135,7 +135,7 @@ def test_semigroup_and_symmetry():
     assert abs(lhs - rhs) < 1e-11
 
 
-@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("n", [2, 3, 4])
 def test_maximum_principle(n):
     """Prop. 3.2: diffusing an O_n field gives sigma_max <= 1 and |det| <= 1."""
     dims = (32, 32)
@@ -304,7 +304,7 @@ def test_energy_forms_agree_and_nonnegative():
         assert e1 == pytest.approx(e2, rel=1e-12)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3])
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
 def test_lyapunov_non_increasing_and_flip_distance(n):
     """Prop. 4.3: E^tau(A_{s+1}) <= E^tau(A_s).  Lemma 4.5: a point whose
     determinant sign flips moves by >= 2 in Frobenius norm."""
@@ -380,6 +380,34 @@ def test_block_embedding_n3_equals_n2_plus_n1():
         assert np.max(np.abs(F[[0, 1, 3, 4]] - A2)) < 1e-12
         assert np.max(np.abs(F[8] - s)) < 1e-12
         assert np.max(np.abs(F[[2, 5, 6, 7]])) < 1e-12
+
+
+def test_block_embedding_n4_equals_two_n2():
+    """blockdiag(R(x), S(x)) with R, S two independent n = 2 fields evolves as
+    the two n = 2 fields: diffusion acts channel by channel and the polar
+    factor of a block-diagonal matrix is the block diagonal of the blocks'
+    polar factors (Lemma 1.1; the 4 x 4 class is the product of the blocks')."""
+    dims = (24, 24)
+    tau = 4.0 / 24 ** 2
+    R = O.project(I.gaussian(dims, 2, 63), 2)
+    S = O.project(I.gaussian(dims, 2, 64), 2)
+    blk = [(0, 0, 0), (0, 1, 1), (1, 0, 2), (1, 1, 3)]  # (i, j, channel of the 2x2)
+
+    def embed(R, S):
+        F = np.zeros((16,) + dims)
+        for i, j, c in blk:
+            F[i * 4 + j] = R[c]
+            F[(i + 2) * 4 + (j + 2)] = S[c]
+        return F
+
+    F = embed(R, S)
+    off = [i * 4 + j for i in range(4) for j in range(4) if (i < 2) != (j < 2)]
+    for _ in range(4):
+        F, _ = O.step(F, 4, tau)
+        R, _ = O.step(R, 2, tau)
+        S, _ = O.step(S, 2, tau)
+        assert np.max(np.abs(F - embed(R, S))) < 1e-12
+        assert np.max(np.abs(F[off])) < 1e-12
 
 
 def test_run_loop_bookkeeping():
