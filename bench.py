@@ -443,6 +443,79 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def run_3d(args, ws, rank, local):
+    """The 3-D workloads (256^3 Voronoi, 512^3 smooth SO(3); n = 3, FP32): K
+    steady-state steps between CUDA events.  The field is larger than L2, so
+    no flush is needed.  One JSON line on rank 0."""
+    import torch
+
+    from paper_1711_01365_gb300 import build as B
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_1711_01365_gb300 import mbo as M
+
+    name = args.workload
+    F, n, tau = I.config_field(name, dtype=np.float32)
+    dims = tuple(F.shape[1:])
+    P = int(np.prod(dims))
+    h = M.Mbo(dims, n, tau, "f32")
+    raw = torch.from_numpy(F).cuda()
+    del F
+    A = torch.empty_like(raw)
+    h.project(raw, A)
+    del raw
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    h.step(A)
+    for _ in range(max(args.warmup - 1, 0)):
+        h.step(A, flags=M.MBO_STEP_CONTINUE)
+    barrier()
+    ms, passes = time_steps(torch, h, A, args.steps, lambda: None)
+    barrier()
+    clocks = clk.stop()
+    value, t = job_throughput(P, args.steps, sum(ms) / 1e3, device="cuda")
+    hbm, peak_kind = load_peaks()
+    C, Q, nx = n * n, (n * n + 1) // 2, dims[-1]
+    xh = min(nx, ((nx // 2 + 1 + 15) // 16) * 16) if (C % 2 and nx in (256, 512, 1024)) else nx
+    w_bytes = ((Q - 1) * nx + xh) * (P // nx) * 2 * 4
+    row_alg = 2 * w_bytes + 2 * C * P * 4
+    col_alg = 2 * w_bytes
+    pt = {k: v[0] / 1e3 / max(v[1], 1) for k, v in passes.items() if v[1]}
+    row_t = pt["row_project"]
+    roofline = {"bound": "hbm", "kernel": "row_project", "achieved": row_alg / row_t / 1e9,
+                "peak": hbm, "unit": "GB/s", "frac": row_alg / row_t / 1e9 / hbm,
+                "peak_kind": peak_kind, "traffic": None,
+                "alg_bytes_per_launch": row_alg, "launch_us": row_t * 1e6,
+                "passes_us": {k: v * 1e6 for k, v in pt.items()},
+                "step_alg_bytes": row_alg + 3 * col_alg,
+                "step_frac": (row_alg + 3 * col_alg) / (t / args.steps) / 1e9 / hbm}
+    if rank == 0:
+        init = {"C3": "Voronoi rotations + N(0,0.05) noise, projected",
+                "C5": "smooth SO(3) field with 20% reflections, projected"}[name]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"3-D flat torus {'x'.join(map(str, dims))}, n=3, tau=2h^2, {init}",
+                           "grid": list(dims), "n": n, "tau": tau,
+                           "l2": "field larger than L2 (no flush)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": None,
+                "e2e": None, "gpu_launches": 4 * args.steps, "clocks": clocks,
+                "note": "secondary workload; cpu_baseline and e2e are measured on the 1024^2 headline only"}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,12 +527,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C5"],
+                    help="C2: 1024^2 headline (default); C3: 256^3, C5: 512^3 (FP32 only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload != "C2":
+        run_3d(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -22,10 +22,13 @@ namespace {
 __host__ __device__ constexpr int wrow_lq(int N) { return N == 1024 ? 32 : 16; }
 __host__ __device__ constexpr int wrow_rb(int N) { return N == 1024 ? 1 : 2; }  // rows per block: whole warps
 
-// Blocks per SM the register budget is sized for (n <= 3: 160-thread blocks
-// at 96 registers; n = 4: 256-thread blocks at 128).
+// Blocks per SM the register budget is sized for (x pass, n <= 3: 160-thread
+// blocks at 96 registers; n = 4: 256-thread blocks at 128; strided passes:
+// 128 registers whatever the tile).
 __host__ __device__ constexpr int wrow_minb(int N, int NM) { return N > 0 && NM <= 3 ? 4 : 2; }
-__host__ __device__ constexpr int wcol_minb(int L, int TX) { return L > 0 && TX == 8 ? 2 : 3; }
+__host__ __device__ constexpr int wcol_minb(int L, int TX) {
+  return 512 / (TX * (L == 1024 ? 32 : 16)) > 0 ? 512 / (TX * (L == 1024 ? 32 : 16)) : 1;
+}
 
 template <int NM, int MODE, int N>
 __global__ void __launch_bounds__(wrow_rb(N) * ((NM * NM + 1) / 2) * wrow_lq(N), wrow_minb(N, NM))

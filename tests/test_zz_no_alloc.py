@@ -30,7 +30,7 @@ def M():
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("dims,n", [((96, 128), 3), ((8, 12, 16), 2), ((64, 64), 1)])
+@pytest.mark.parametrize("dims,n", [((96, 128), 3), ((8, 12, 16), 2), ((64, 64), 1), ((48, 64), 4)])
 def test_noalloc_matches_mbo_diffuse_on_two_calls_in_a_row(M, dims, n, dtype):
     tau = 3.0 / max(dims) ** 2
     tdt = torch.float32 if dtype == "f32" else torch.float64
