@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmbo_gb300.so")
-SOURCES = ["mbo_api.cu", "k_f32.cu", "k_f64.cu", "k_warp.cu", "k_select.cu", "mbo_noalloc.cu"]
+SOURCES = ["mbo_api.cu", "k_f32.cu", "k_f64.cu", "k_warp.cu", "k_wcol.cu", "k_select.cu", "mbo_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

@@ -87,7 +87,8 @@ Plan axis_plan(const Geom& g, int axis, bool f32) {
       (axis == 0 || axis < g.ndim)) {
     Plan p{};
     p.len = N;
-    p.lq = N == 1024 ? 32 : 16;
+    p.rad0 = warp_plan_radix(N);
+    p.lq = N / p.rad0 == 1024 ? 32 : 16;
     return p;
   }
   return make_plan(N);
@@ -237,13 +238,23 @@ void build_tables(mbo_ctx* h, TabBuild<R>& tb, Tables<R>& t) {
     const int N = lens[ax];
     const Plan& pl = t.plan[ax];
     R* tw = reinterpret_cast<R*>(&tb.bytes[tb.off_tw[ax]]);
-    if (pl.lq) {  // [k2][l] = exp(-2 pi i l k2 / N)
-      const int E = N / pl.lq;
+    if (pl.lq) {
+      // N = rad0 * Mw: the length-Mw table [k2][l] = exp(-2 pi i l k2 / Mw), then
+      // the pre-stage twiddles exp(-2 pi i r k' / N) at Mw + (r - 1) Mw + k'
+      const int Mw = N / pl.rad0, E = Mw / pl.lq;
       for (int k2 = 0; k2 < E; ++k2)
         for (int l = 0; l < pl.lq; ++l) {
-          const long long e = ((long long)l * k2) % N;
-          const double ang = 2.0 * pi * (double)e / (double)N;
+          const long long e = ((long long)l * k2) % Mw;
+          const double ang = 2.0 * pi * (double)e / (double)Mw;
           const size_t i = (size_t)k2 * pl.lq + l;
+          tw[2 * i] = (R)std::cos(ang);
+          tw[2 * i + 1] = (R)(-std::sin(ang));
+        }
+      for (int r = 1; r < pl.rad0; ++r)
+        for (int k = 0; k < Mw; ++k) {
+          const long long e = ((long long)r * k) % N;
+          const double ang = 2.0 * pi * (double)e / (double)N;
+          const size_t i = (size_t)Mw + (size_t)(r - 1) * Mw + k;
           tw[2 * i] = (R)std::cos(ang);
           tw[2 * i + 1] = (R)(-std::sin(ang));
         }

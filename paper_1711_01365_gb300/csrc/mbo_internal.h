@@ -36,14 +36,17 @@ struct Stage {
 // Transform plan of one axis.
 //   lq == 0: the in-place network of nst stages (forward stages applied in
 //            order, product = N); the spectrum is left digit-reversed.
-//   lq >  0: the warp-cooperative four-step transform of N = lq * (N / lq)
-//            points held in registers by lq lanes per sequence; the spectrum
-//            is in natural order and the twiddle table holds
-//            exp(-2 pi i l k2 / N) at [k2][l] (k2 < N / lq, l < lq).
+//   lq >  0: the warp-cooperative four-step transform of M = lq * (M / lq)
+//            points held in registers by lq lanes per sequence, N = rad0 * M
+//            (rad0 > 1: rad0 such sequences combined by a length-rad0 DFT);
+//            the spectrum is in natural order and the twiddle table holds
+//            exp(-2 pi i l k2 / M) at [k2][l] (k2 < M / lq, l < lq), then
+//            exp(-2 pi i r k / N) at M + (r - 1) M + k (0 < r < rad0, k < M).
 struct Plan {
   int nst;
   int lq;
-  int len;  // N
+  int len;   // N
+  int rad0;  // warp plans: N = rad0 * M with a length-M warp transform (rad0 in 1..3)
   Stage st[kMaxStages];
 };
 
@@ -184,13 +187,15 @@ bool factor23(int64_t N, int& a, int& b);
 FastDiv make_div(unsigned d);
 Plan make_plan(int N);
 // Plan of one axis of a geometry: the warp-cooperative plan (FP32, lengths
-// 256, 512, 1024; strided axes need nx % 4 == 0) where one exists, else make_plan.
+// 256, 512, 768, 1024, 1536, 2048; strided axes need nx % 4 == 0) where one
+// exists, else make_plan.
 Plan axis_plan(const Geom& g, int axis, bool f32);
 int plan_twiddles(const Plan& p);
 int pick_tx(int nx, int cap);
 
 // FP32 passes over warp-plan axes (k_warp.cu).
 bool warp_plan_length(int N);
+int warp_plan_radix(int N);
 int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4 or 8; 0: none)
 size_t wrow_smem_bytes(const Geom& g, int N, bool fallback);
 size_t wcol_smem_bytes(int L, int tx);

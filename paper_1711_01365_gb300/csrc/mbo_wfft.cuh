@@ -134,3 +134,86 @@ template <int N, int LQ> struct WarpFFT {
 };
 
 }  // namespace mbo
+
+namespace mbo {
+
+// Lengths N = R * M (R = 2 or 3, M one of the lengths above): R groups of LQ
+// lanes, group r holding the sub-sequence a[R x' + r] (x' = l + LQ j), run the
+// length-M transform; a twiddle W_N^(r k') and a length-R DFT across the groups,
+// through shared memory, complete it:
+//   X[k' + M s] = sum_r W_R^(r s) W_N^(r k') Y_r[k'],   Y_r = DFT_M(a[R x' + r]),
+// so group s ends up holding X[k' + M s] (k' = l + LQ j): natural order again.
+// The inverse runs the steps transposed and conjugated.  Group r works in the
+// r-th of R consecutive regions of RS slots; for R > 1 the cross-group steps
+// end with a block barrier, so every thread of the block must call them.  For
+// R = 1 the calls are those of WarpFFT.
+template <int M, int LQ, int R> struct WarpFFTR {
+  using F = WarpFFT<M, LQ>;
+  static constexpr int E = F::E;
+  static constexpr int RS = F::RS;
+
+  // W_R^(e) for a constant e
+  template <typename V> __device__ __forceinline__ static V rot(V a, int e) {
+    e %= R;
+    if (R == 2) return e ? V{-a.x, -a.y} : a;
+    constexpr float h = 0.86602540378443864676f;  // sqrt(3)/2, W_3 = -1/2 - i h
+    if (e == 0) return a;
+    const float s = (e == 1) ? -h : h;  // Im W_3^e
+    return V{-0.5f * a.x - s * a.y, -0.5f * a.y + s * a.x};
+  }
+
+  // tw: the length-M table [k2][l]; twr: W_N^(r k') at [(r - 1) * M + k'].
+  template <typename V>
+  __device__ __forceinline__ static void fwd(V (&v)[E], V* base, int r, const V* __restrict__ tw,
+                                             const V* __restrict__ twr, int l) {
+    if constexpr (R == 1) {
+      F::fwd(v, base, tw, l);
+      return;
+    }
+    F::fwd(v, base + r * RS, tw, l);
+    if (r > 0) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&twr[(r - 1) * M + l + LQ * j]));
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) base[r * RS + l + LQ * j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      V acc = base[l + LQ * j];
+#pragma unroll
+      for (int rr = 1; rr < R; ++rr) acc = cadd(acc, rot(base[rr * RS + l + LQ * j], rr * r));
+      v[j] = acc;
+    }
+    __syncthreads();
+  }
+
+  // group s holds X[k' + M s]  ->  group r holds sum_k X[k] exp(+2 pi i (R x' + r) k / N)
+  template <typename V>
+  __device__ __forceinline__ static void inv(V (&v)[E], V* base, int r, const V* __restrict__ tw,
+                                             const V* __restrict__ twr, int l) {
+    if constexpr (R == 1) {
+      F::inv(v, base, tw, l);
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) base[r * RS + l + LQ * j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      V acc = base[l + LQ * j];
+#pragma unroll
+      for (int s = 1; s < R; ++s) acc = cadd(acc, rot(base[s * RS + l + LQ * j], (R - 1) * s * r));
+      if (r > 0) {
+        V c = __ldg(&twr[(r - 1) * M + l + LQ * j]);
+        c.y = -c.y;
+        acc = cmul(acc, c);
+      }
+      v[j] = acc;
+    }
+    __syncthreads();
+    F::inv(v, base + r * RS, tw, l);
+  }
+};
+
+}  // namespace mbo

@@ -1,0 +1,35 @@
+// Shapes and launch helpers shared by the FP32 warp-plan passes (k_warp.cu,
+// k_wcol.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mbo {
+
+// Length N = R * M with M in {256, 512, 1024} and R in {1, 2, 3} (see WarpFFTR).
+inline __host__ __device__ constexpr int w_r(int N) { return N % 3 == 0 ? 3 : (N > 1024 ? 2 : 1); }
+inline __host__ __device__ constexpr int w_m(int N) { return N / w_r(N); }
+inline __host__ __device__ constexpr int w_lq(int N) { return w_m(N) == 1024 ? 32 : 16; }
+inline __host__ __device__ constexpr int wrow_rb(int N) { return w_lq(N) == 32 ? 1 : 2; }  // rows per block: whole warps
+inline __host__ __device__ constexpr int wrow_threads(int N, int NM) {
+  return wrow_rb(N) * ((NM * NM + 1) / 2) * w_r(N) * w_lq(N);
+}
+
+// Blocks per SM the register budget is sized for: the x pass at 96 registers
+// (n <= 3) or 128 (n = 4), the strided passes at 128.
+inline __host__ __device__ constexpr int wrow_minb(int N, int NM) {
+  return 65536 / (wrow_threads(N, NM) * (NM <= 3 ? 96 : 128)) > 0
+             ? 65536 / (wrow_threads(N, NM) * (NM <= 3 ? 96 : 128))
+             : 1;
+}
+inline __host__ __device__ constexpr int wcol_minb(int L, int TX) {
+  return 512 / (TX * w_r(L) * w_lq(L)) > 0 ? 512 / (TX * w_r(L) * w_lq(L)) : 1;
+}
+
+template <typename K> inline cudaError_t set_smem_once(K kernel, size_t bytes, size_t& done) {
+  if (bytes <= 48 * 1024 || bytes <= done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = bytes;
+  return e;
+}
+
+}  // namespace mbo

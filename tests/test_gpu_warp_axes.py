@@ -1,5 +1,6 @@
-"""FP32 axes of length 256, 512 and 1024, which the library transforms with the
-warp-cooperative four-step plan (spectrum in natural order), against the
+"""FP32 axes of length 256, 512 and 1024, and 768, 1536 and 2048 (a radix-3 or
+radix-2 stage across groups of lanes on top), which the library transforms with
+the warp-cooperative four-step plan (spectrum in natural order), against the
 oracle: the diffusion (Sec. 5.1), one step of Algorithm 1 and a second step
 from the kept spectrum, and the Lyapunov functional of Sec. 4.
 
@@ -33,6 +34,15 @@ WARP_SHAPES = [
     (256, 2, 8),     # 3-D: z
     (2, 4, 512),     # 3-D: x
     (256, 4, 256),   # 3-D: z and x
+    (4, 2048),       # x: 2 groups of 32 lanes (radix-2 stage)
+    (3, 1536),       # x: 3 groups of 16 lanes (radix-3 stage), odd row count
+    (6, 768),        # x: 3 x 256
+    (2048, 4),       # y: 2 x 1024, 4-column tiles
+    (1536, 8),       # y: 3 x 512
+    (768, 16),       # y: 3 x 256
+    (768, 768),      # y and x
+    (768, 2, 8),     # 3-D: z
+    (2, 4, 1536),    # 3-D: x
 ]
 
 
