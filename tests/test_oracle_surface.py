@@ -1,0 +1,188 @@
+"""Pins of the closed-surface oracle (oracle/surface.py) against what the paper
+and the mathematics fix (Sec. 5.2, Algorithm 2, Tables 1 and 2, Sec. 6.2):
+
+* the tail bound T against the radial integral of the 3-D heat kernel it
+  bounds, and the band widths against Table 1 and the widths the sphere,
+  peanut and volume-constrained sphere experiments print;
+* the spectral heat-kernel approximation against the exact Gaussian, within
+  the theorem's error bound, for the theorem's mode counts (never below those
+  of Table 2) at the time steps of the paper's surface experiments;
+* the quadrature rule against Fejer's closed form and polynomial exactness;
+* the sphere's closest-point map against brute force;
+* the plain double sum of Algorithm 2 against the exact Gaussian convolution it
+  approximates (tensor-product form of the theorem's bound);
+* the closest-point diffusion on the unit sphere: constants are kept, and the
+  degree-1 harmonic z decays at the Laplace-Beltrami rate 1 - 2 tau to first
+  order in tau;
+* one surface step of a constant rotation field returns that rotation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import surface as S
+
+TAUS = [1e-1, 1e-2, 1e-3, 1e-4]
+EPSS = [1e-3, 1e-6, 1e-9, 1e-12]
+# Table 1: band width w_b for (eps, tau)
+TABLE1 = [[1.796, 0.5683, 0.1796, 0.05683],
+          [2.474, 0.7823, 0.2474, 0.07823],
+          [2.993, 0.9465, 0.2993, 0.09465],
+          [3.432, 1.085, 0.3432, 0.1085]]
+# Table 2: number of Fourier modes M for (eps, tau), R = pi
+TABLE2 = [[8, 21, 55, 136],
+          [11, 34, 100, 296],
+          [14, 43, 130, 396],
+          [17, 50, 154, 475]]
+
+
+def test_tail_bound_is_the_gaussian_tail_integral():
+    quad = pytest.importorskip("scipy.integrate").quad
+    for tau in (0.01, 0.2):
+        for wb in (0.1, 0.5, 1.3):
+            g = lambda r: 4 * math.pi * r * r * math.exp(-r * r / (4 * tau)) / (4 * math.pi * tau) ** 1.5
+            tail = quad(g, wb, math.inf, epsabs=1e-15, epsrel=1e-12)[0]
+            assert S.T(wb / (2 * math.sqrt(tau))) == pytest.approx(tail, rel=1e-9, abs=1e-15)
+
+
+def test_band_width_against_table1_and_the_experiments():
+    # Table 1 solves the leading term 2x/sqrt(pi) e^{-x^2} = eps; the full bound
+    # T adds erfc(x) > 0, so the oracle's width is never smaller, and within 0.5 %
+    for i, eps in enumerate(EPSS):
+        for j, tau in enumerate(TAUS):
+            wb = S.band_width(eps, tau)
+            assert S.T(wb / (2 * math.sqrt(tau))) == pytest.approx(eps, rel=1e-9)
+            r = wb / TABLE1[i][j]
+            assert 1.0 - 6e-4 <= r <= 1.005, (eps, tau, wb)
+    # Sec. 6.2 (sphere, tau = 0.005), Sec. 6.3 (peanut, tau = 0.032), Sec. 7
+    # (sphere with volume constraint, tau = 0.01), all at eps = 1e-6
+    for tau, printed in ((0.005, 0.5532), (0.032, 1.3994), (0.01, 0.7823)):
+        r = S.band_width(1e-6, tau) / printed
+        assert 1.0 - 1e-4 <= r <= 1.002
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_heat_kernel_approximation_meets_the_theorem_bound(i):
+    eps = EPSS[i]
+    x = np.linspace(-math.pi, math.pi, 2001)
+    for j, tau in enumerate(TAUS):
+        h, M = S.heat_modes(eps, tau, math.pi)
+        assert TABLE2[i][j] <= M <= TABLE2[i][j] * 1.2 + 2
+    # the bound |G_tau - sum| <= 4 eps / sqrt(4 pi tau) on |x| <= R holds with the
+    # theorem's M for h^2 tau >= 0.005 (every experiment of Sec. 6.2-7: tau from
+    # 0.005 to 0.032 at h <= 1); below that the printed M falls short of it
+    for tau in (0.1, 0.032, 0.01, 0.005):
+        h, M = S.heat_modes(eps, tau, math.pi)
+        bound = 4 * eps / math.sqrt(4 * math.pi * tau)
+        err = np.abs(S.kernel_1d(x, tau, h, M) - S.gauss_1d(x, tau)).max()
+        assert err <= bound, (eps, tau, M, err, bound)
+        # a plausible slip (half the modes) breaks it
+        err2 = np.abs(S.kernel_1d(x, tau, h, M // 2) - S.gauss_1d(x, tau)).max()
+        assert err2 > bound
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 7])
+def test_cheb_rule_is_fejer_and_exact(p):
+    t, w = S.cheb_rule(p)
+    th = (2 * np.arange(1, p + 1) - 1) * np.pi / (2 * p)
+    # nodes are the zeros of T_p
+    assert np.abs(np.cos(p * np.arccos(t))).max() < 1e-12
+    # Fejer's first rule in closed form
+    fej = np.array([(2.0 / p) * (1 - 2 * sum(np.cos(2 * j * a) / (4 * j * j - 1) for j in range(1, p // 2 + 1)))
+                    for a in th])
+    assert np.abs(w - fej).max() < 1e-12
+    for deg in range(p):
+        exact = (1 - (-1) ** (deg + 1)) / (deg + 1)
+        assert (w * t ** deg).sum() == pytest.approx(exact, abs=1e-12)
+
+
+def test_sphere_closest_point_is_the_nearest_sphere_point():
+    g = np.random.default_rng(5)
+    x = g.uniform(-2, 2, (40, 3))
+    r = 1.3
+    c = S.sphere_closest(x, r)
+    assert np.allclose(np.linalg.norm(c, axis=1), r)
+    u = g.standard_normal((20000, 3))
+    sph = r * u / np.linalg.norm(u, axis=1, keepdims=True)
+    d_brute = np.sqrt(((x[:, None, :] - sph[None, :, :]) ** 2).sum(-1)).min(1)
+    d = np.linalg.norm(x - c, axis=1)
+    assert np.all(d <= d_brute + 1e-12)
+    assert np.all(np.abs(d - np.abs(np.linalg.norm(x, axis=1) - r)) < 1e-12)
+
+
+def test_sphere_band_cells_and_weights():
+    r, dx, wb, p = 1.0, 0.25, 0.4, 2
+    xq, wq, xc = S.sphere_band(r, dx, wb, p)
+    # brute force: the cell corners of dx Z^3 within wb of the sphere
+    n = 0
+    for i in range(-8, 9):
+        for j in range(-8, 9):
+            for k in range(-8, 9):
+                if abs(math.sqrt(i * i + j * j + k * k) * dx - r) < wb:
+                    n += 1
+    assert xq.shape == (n * p ** 3, 3)
+    assert wq.sum() == pytest.approx(n * dx ** 3, rel=1e-12)
+    corners = dx * np.floor(xq / dx + 1e-9)
+    assert np.all(np.abs(np.linalg.norm(corners, axis=1) - r) < wb)
+    assert np.allclose(np.linalg.norm(xc, axis=1), r)
+
+
+def test_double_sum_against_exact_gaussian_within_the_bound():
+    g = np.random.default_rng(11)
+    xs = g.uniform(0, 1, (400, 3))
+    xt = g.uniform(0, 1, (60, 3))
+    ws = g.uniform(0.5, 1.5, 400) / 400
+    F = g.standard_normal((2, 400))
+    tau, eps = 0.01, 1e-6
+    R = S.extent(xs, xt)
+    h, M = S.heat_modes(eps, tau, R)
+    got = S.surface_diffuse(F, xs, ws, xt, tau, h, M)
+    ref = S.gauss_convolve(F, xs, ws, xt, tau)
+    e1 = 4 * eps / math.sqrt(4 * math.pi * tau)
+    g1 = 1 / math.sqrt(4 * math.pi * tau)
+    bound3 = 3 * e1 * (g1 + e1) ** 2
+    tot = (np.abs(F) * ws[None, :]).sum(1)
+    err = np.abs(got - ref).max(1)
+    assert np.all(err <= tot * bound3)
+    assert np.abs(ref).max() > 100 * err.max()
+    # a dropped heat factor, a flipped phase sign or a wrong prefactor is far off
+    bad = S.surface_diffuse(F, xs, ws, xt, tau * 0.5, h, M)
+    assert np.abs(bad - ref).max() > 1e3 * err.max()
+    bad2 = S.surface_diffuse(F, xs, ws, -xt, tau, h, M)
+    assert np.abs(bad2 - S.gauss_convolve(F, xs, ws, -xt, tau)).max() > 1e3 * err.max()
+
+
+def test_closest_point_diffusion_on_the_unit_sphere():
+    tau, eps, dx, p = 0.01, 1e-6, 0.1, 2
+    wb = S.band_width(eps, tau)
+    xq, wq, xc = S.sphere_band(1.0, dx, wb, p)
+    idx = np.random.default_rng(3).choice(len(xq), 40, replace=False)
+    one = S.gauss_convolve(np.ones((1, len(xq))), xq, wq, xc[idx], tau)
+    assert np.abs(one - 1).max() < 1e-5
+    z = S.gauss_convolve(xc[:, 2][None, :], xq, wq, xc[idx], tau)[0]
+    sel = np.abs(xc[idx, 2]) > 0.2
+    ratio = z[sel] / xc[idx, 2][sel]
+    # Delta_S z = -2 z on the unit sphere: decay 1 - 2 tau + O(tau^2)
+    assert np.abs(ratio - (1 - 2 * tau)).max() < tau * tau
+
+
+def test_surface_step_keeps_a_constant_rotation():
+    # small band, small mode count: the double sum stays cheap
+    tau, eps, dx, p = 0.04, 1e-3, 0.25, 1
+    wb = S.band_width(eps, tau)
+    xq, wq, xc = S.sphere_band(1.0, dx, wb, p)
+    h, M = S.heat_modes(eps, tau, S.extent(xq, xc))
+    Q = np.linalg.qr(np.random.default_rng(2).standard_normal((3, 3)))[0]
+    A = np.repeat(Q.reshape(9, 1), len(xq), axis=1)
+    B, At, st = S.surface_step(A, xq, wq, xc, 3, tau, h, M)
+    assert np.abs(B - A).max() < 1e-10
+    assert st["det_flips"] == 0
+    # the diffused field is a positive multiple of Q (close to 1: the band holds the ball)
+    c = At[0] / Q[0, 0]
+    assert np.abs(At - np.outer(Q.reshape(9), c)).max() < 1e-10
+    assert np.all(np.abs(c - 1) < 0.05)
+    Bm = B[:, 0].reshape(3, 3)
+    assert np.abs(Bm @ Bm.T - np.eye(3)).max() < 1e-12
+    assert O.det(Bm) == pytest.approx(np.linalg.det(Q), abs=1e-12)
