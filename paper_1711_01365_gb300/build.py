@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmbo_gb300.so")
-SOURCES = ["mbo_api.cu", "k_f32.cu", "k_f64.cu", "k_warp.cu", "k_wcol.cu", "k_select.cu", "mbo_noalloc.cu"]
+SOURCES = ["mbo_api.cu", "k_f32.cu", "k_f64.cu", "k_warp.cu", "k_wcol.cu", "k_select.cu", "mbo_noalloc.cu",
+           "mbo_surface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]
@@ -32,6 +33,7 @@ def _nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(ROOT, "include", "mbo.h"))
+    files.append(os.path.join(ROOT, "include", "mbo_surface.h"))
     return files
 
 

@@ -985,6 +985,42 @@ struct mbo_batch_ctx {
   char err[512] = {0};
 };
 
+namespace mbo {
+
+bool set_axis_multipliers(mbo_ctx* h, const double* const* mult) {
+  if (!h || !mult) return false;
+  DeviceGuard dg(h->dev);
+  const int lens[3] = {h->g.nx, h->g.ny, h->g.nz};
+  const bool f32 = h->dtype == MBO_F32;
+  for (int ax = 0; ax < h->g.ndim; ++ax) {
+    if (!mult[ax]) return false;
+    const int N = lens[ax];
+    const Plan& pl = f32 ? h->tf.plan[ax] : h->td.plan[ax];
+    std::vector<int> pos;
+    digit_positions(pl, N, pos);
+    std::vector<double> g(N), om(N);
+    for (int k = 0; k < N; ++k) {
+      g[pos[k]] = mult[ax][k];
+      om[pos[k]] = 1.0 - mult[ax][k];
+    }
+    cudaError_t e;
+    if (f32) {
+      std::vector<float> gf(g.begin(), g.end()), of(om.begin(), om.end());
+      e = cudaMemcpy(const_cast<float*>(h->tf.g[ax]), gf.data(), N * sizeof(float), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(const_cast<float*>(h->tf.om[ax]), of.data(), N * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+      e = cudaMemcpy(const_cast<double*>(h->td.g[ax]), g.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(const_cast<double*>(h->td.om[ax]), om.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return false;
+  }
+  return true;
+}
+
+}  // namespace mbo
+
 namespace {
 
 constexpr int kBatchStreams = 8;

@@ -211,6 +211,13 @@ cudaError_t launch_volume(int which, const Geom& g, const R* At, R* A, unsigned 
                           SelectState* ss, const StatsPtrs& sp, double fb, int blocks,
                           cudaStream_t s);
 
+// Replace the per-axis multipliers of a handle's diffusion (mbo_api.cu).
+// mult[ax] (ax = 0: x, 1: y, 2: z; z ignored in 2-D) holds N_ax values in
+// natural frequency order: index k is the signed frequency k (2k <= N) or
+// k - N.  The diffusion then multiplies spectrum entry (kz, ky, kx) by
+// mult[2][kz] mult[1][ky] mult[0][kx] / P.  Host; synchronous.
+bool set_axis_multipliers(struct mbo_ctx* h, const double* const* mult);
+
 // Shared memory bytes of the row kernel for a geometry.
 size_t row_smem_bytes(const Geom& g, size_t elem_bytes, bool fallback);
 size_t axis_smem_bytes(int len, int tx, size_t elem_bytes);

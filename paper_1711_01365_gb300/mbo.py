@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI in ``include/mbo.h``.
+"""Thin ctypes binding of the C ABI in ``include/mbo.h`` and ``include/mbo_surface.h``.
 
 Every function keeps the C name and only marshals arguments: tensors become
 device (or, for the run loop, host) pointers, streams become ``cudaStream_t``
@@ -33,6 +33,11 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
            "mbo_batch_step", "mbo_batch_run", "mbo_batch_workspace_bytes", "mbo_batch_last_error",
            "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
 
+SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
+                   "mbo_surface_create", "mbo_surface_destroy", "mbo_surface_get_params",
+                   "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_workspace_bytes",
+                   "mbo_surface_last_error")
+
 MBO_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 PASSES = ("row_fwd", "axis_fwd", "axis_fgi", "axis_inv", "axis_energy", "row_project", "row_inv",
@@ -48,6 +53,17 @@ class MboError(RuntimeError):
 class mbo_config(C.Structure):
     _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int),
                 ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int)]
+
+
+class mbo_surface_params(C.Structure):
+    _fields_ = [("h", C.c_double), ("M", C.c_int), ("nf", C.c_int), ("width", C.c_int),
+                ("beta", C.c_double), ("R", C.c_double), ("center", C.c_double * 3),
+                ("bins", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["center"] = tuple(self.center)
+        return d
 
 
 class mbo_stats(C.Structure):
@@ -111,6 +127,26 @@ def lib():
     L.mbo_status_string.restype = C.c_char_p
     L.mbo_last_error.argtypes = [vp]
     L.mbo_last_error.restype = C.c_char_p
+    dp = C.POINTER(C.c_double)
+    L.mbo_surface_band_width.argtypes = [C.c_double, C.c_double]
+    L.mbo_surface_band_width.restype = C.c_double
+    L.mbo_surface_heat_modes.argtypes = [C.c_double, C.c_double, C.c_double, dp, C.POINTER(C.c_int)]
+    L.mbo_surface_sphere_band.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, vp, vp, vp,
+                                          C.c_int64, i64p]
+    L.mbo_surface_create.argtypes = [C.POINTER(vp), C.c_int64, vp, vp, vp, C.c_int, C.c_double,
+                                     C.c_double, C.c_int]
+    L.mbo_surface_destroy.argtypes = [vp]
+    L.mbo_surface_get_params.argtypes = [vp, C.POINTER(mbo_surface_params)]
+    L.mbo_surface_diffuse.argtypes = [vp, vp, vp, vp]
+    L.mbo_surface_step.argtypes = [vp, vp, C.POINTER(mbo_stats), vp]
+    L.mbo_surface_workspace_bytes.argtypes = [vp]
+    L.mbo_surface_workspace_bytes.restype = C.c_int64
+    L.mbo_surface_last_error.argtypes = [vp]
+    L.mbo_surface_last_error.restype = C.c_char_p
+    for f in ("mbo_surface_heat_modes", "mbo_surface_sphere_band", "mbo_surface_create",
+              "mbo_surface_destroy", "mbo_surface_get_params", "mbo_surface_diffuse",
+              "mbo_surface_step"):
+        getattr(L, f).restype = C.c_int
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
               "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
               "mbo_diffuse_noalloc", "mbo_step_volume", "mbo_run_volume", "mbo_batch_create",
@@ -393,3 +429,104 @@ class Mbo:
 
     def run_volume(self, A, n_plus: int, max_steps: int, tol: float, stream=None) -> dict:
         return mbo_run_volume(self.h, A, n_plus, max_steps, tol, stream)
+
+
+# ---------------------------------------------------------------------------
+# closed surfaces (include/mbo_surface.h)
+# ---------------------------------------------------------------------------
+
+def _scheck(rc: int, s=None) -> None:
+    if rc != 0:
+        msg = lib().mbo_status_string(rc).decode()
+        if s is not None:
+            detail = lib().mbo_surface_last_error(s).decode()
+            if detail:
+                msg += f" ({detail})"
+        raise MboError(rc, msg)
+
+
+def mbo_surface_band_width(eps: float, tau: float) -> float:
+    return float(lib().mbo_surface_band_width(float(eps), float(tau)))
+
+
+def mbo_surface_heat_modes(eps: float, tau: float, R: float):
+    h, M = C.c_double(), C.c_int()
+    _scheck(lib().mbo_surface_heat_modes(float(eps), float(tau), float(R), C.byref(h), C.byref(M)))
+    return h.value, M.value
+
+
+def mbo_surface_sphere_band(radius: float, dx: float, wb: float, p: int):
+    """(xq, wq, xc) host arrays of the sphere band (count query, then fill)."""
+    cnt = C.c_int64()
+    _scheck(lib().mbo_surface_sphere_band(float(radius), float(dx), float(wb), int(p), None, None,
+                                          None, 0, C.byref(cnt)))
+    n = cnt.value
+    xq, wq, xc = np.empty((n, 3)), np.empty(n), np.empty((n, 3))
+    _scheck(lib().mbo_surface_sphere_band(float(radius), float(dx), float(wb), int(p), xq.ctypes.data,
+                                          wq.ctypes.data, xc.ctypes.data, n, C.byref(cnt)))
+    return xq, wq, xc
+
+
+def mbo_surface_create(xq, wq, xc, n: int, tau: float, eps: float, dtype: int = MBO_F32):
+    xq = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
+    xc = np.ascontiguousarray(xc, dtype=np.float64).reshape(-1, 3)
+    wq = np.ascontiguousarray(wq, dtype=np.float64).reshape(-1)
+    s = C.c_void_p()
+    _scheck(lib().mbo_surface_create(C.byref(s), xq.shape[0], xq.ctypes.data, wq.ctypes.data,
+                                     xc.ctypes.data, int(n), float(tau), float(eps), int(dtype)))
+    return s
+
+
+def mbo_surface_destroy(s) -> None:
+    _scheck(lib().mbo_surface_destroy(s))
+
+
+def mbo_surface_get_params(s) -> dict:
+    p = mbo_surface_params()
+    _scheck(lib().mbo_surface_get_params(s, C.byref(p)), s)
+    return p.as_dict()
+
+
+def mbo_surface_diffuse(s, A, A_tilde, stream=None) -> None:
+    _scheck(lib().mbo_surface_diffuse(s, _ptr(A), _ptr(A_tilde), _stream(stream)), s)
+
+
+def mbo_surface_step(s, A, want_stats: bool = False, stream=None):
+    st = mbo_stats()
+    _scheck(lib().mbo_surface_step(s, _ptr(A), C.byref(st) if want_stats else None, _stream(stream)), s)
+    return st.as_dict() if want_stats else None
+
+
+def mbo_surface_workspace_bytes(s) -> int:
+    return int(lib().mbo_surface_workspace_bytes(s))
+
+
+class Surface:
+    """Owning wrapper of a surface plan.  Fields: tensors of shape (n*n, nq)."""
+
+    def __init__(self, xq, wq, xc, n: int, tau: float, eps: float, dtype: str = "f32"):
+        self.n, self.tau, self.eps = int(n), float(tau), float(eps)
+        self.nq = int(np.asarray(wq).size)
+        self.dtype = {"f32": MBO_F32, "f64": MBO_F64}[dtype]
+        self.h = mbo_surface_create(xq, wq, xc, n, tau, eps, self.dtype)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            mbo_surface_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> dict:
+        return mbo_surface_get_params(self.h)
+
+    def diffuse(self, A, out, stream=None):
+        mbo_surface_diffuse(self.h, A, out, stream)
+        return out
+
+    def step(self, A, want_stats=False, stream=None):
+        return mbo_surface_step(self.h, A, want_stats, stream)

@@ -1,5 +1,5 @@
 """CPU-side checks of the C ABI: the library builds, loads and exports every
-symbol include/mbo.h declares, and argument validation that happens before
+symbol include/mbo.h and include/mbo_surface.h declare, and argument validation that happens before
 any device call rejects bad input with the documented status codes."""
 import os
 import re
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    hdr = open(os.path.join(ROOT, "include", "mbo.h")).read()
+    hdr = "".join(open(os.path.join(ROOT, "include", f)).read() for f in ("mbo.h", "mbo_surface.h"))
     return sorted(set(re.findall(r"MBO_API\s+[\w\s\*]*?\b(mbo_\w+)\s*\(", hdr)))
 
 
@@ -25,9 +25,9 @@ def lib():
 
 def test_header_declares_the_expected_entry_points():
     syms = declared_symbols()
-    for name in M.EXPORTS:
+    for name in M.EXPORTS + M.SURFACE_EXPORTS:
         assert name in syms
-    assert len(syms) >= len(M.EXPORTS)
+    assert len(syms) >= len(M.EXPORTS) + len(M.SURFACE_EXPORTS)
 
 
 def test_library_exports_every_declared_symbol(lib):
