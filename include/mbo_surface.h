@@ -79,8 +79,9 @@ MBO_API mbo_status mbo_surface_sphere_band(double radius, double dx, double wb, 
  *   n         matrix order 1..4; tau > 0 the diffusion time of one step.
  *   eps       accuracy in (1e-12, 1/2): it sets h and M (mbo_surface_heat_modes
  *             with R the largest coordinate extent of all xq and xc) and the
- *             spreading width ceil(log10(1/eps)) + 1 (clamped to 2..12; at most
- *             8 for MBO_F32).
+ *             spreading width ceil(log10(1/eps)) + 1, clamped to 4..8 (the
+ *             spreading error is then about 10^(1 - width): below 1e-7 the
+ *             non-uniform transforms, not eps, set the accuracy).
  * The oversampled grid has nf = the smallest 2^a 3^b >= max(4M, 2 width, 8)
  * points per axis (MBO_ERR_UNSUPPORTED_SIZE above 2048).  Allocates that
  * grid (n*n channels), the library's FFT workspace for it and the sorted

@@ -5,30 +5,38 @@
 //   A~(x_t) = (h/2pi)^3 Re sum_m e^{-h^2 tau |m|^2} e^{i h m.x_t} sum_q w_q A(x_q^c) e^{-i h m.x_q}
 // over m in {-M..M-1}^3.  With theta = h (x - centre) every point lies in
 // [-pi/2, pi/2]^3, and the two non-uniform sums are computed on a periodic grid
-// of nf points per axis (spacing 2 pi / nf, nf >= 4M):
-//   k_spread   type-1 spreading: every source adds w_q A(x_q^c) phi(2 (j - u_q) / W)
-//              to the W^3 grid points j around its grid coordinate u_q, with the
-//              "exponential of semicircle" kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1))
-//              (Barnett, Magland, af Klinteberg, SIAM J. Sci. Comput. 41, 2019).
-//              Sources are sorted into bins of kBin^3 grid cells; one block per
-//              (bin, channel group) accumulates into a shared-memory tile of
-//              (kBin + W)^3 points and adds the tile to the grid at the end.
+// of nf points per axis (spacing 2 pi / nf, nf >= 4M) with the "exponential
+// of semicircle" kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) of width W grid
+// points (Barnett, Magland, af Klinteberg, SIAM J. Sci. Comput. 41, 2019):
+//   k_spread   type-1 spreading: source q adds w_q A(x_q^c) phi(2 (j - u_q) / W) to
+//              the W^3 grid points j around its grid coordinate u_q (phi of a
+//              vector: the product of its three coordinates' factors).
 //   (the library's 3-D FFT diffusion with the per-axis multiplier
 //              nf (h / 2 pi) win(k) e^{-k^2 h^2 tau} / psi(k)^2, psi the kernel's
 //              Fourier transform: forward FFT, multiplier, inverse FFT, in one
 //              call of the torus path)
-//   k_interp   type-2 interpolation: each target sums phi-weighted grid values
-//              around its coordinate (one warp per target, lanes over the W^3
-//              points), then, in the step, a lane per target projects the
-//              matrix (Lemma 1.1) and writes it back with the step statistics.
+//   k_interp   type-2 interpolation: target t sums the phi-weighted grid values
+//              around its coordinate.
+//   k_sproject projection of every target (Lemma 1.1) with the step statistics.
 // win(k) = 1 for |k| < M, 1/2 at |k| = M (the real part of the sum over
 // -M..M-1), 0 beyond.
+//
+// Points that share their nearest grid point share their footprint (the W^3
+// points spread to or read from), and the plan sorts them into such groups
+// once (the geometry is fixed).  Spreading: one warp per group, a lane per
+// footprint column (x, y) holding the W points along z for CG channels in
+// registers; the group's sources are summed there and added once to a
+// shared-memory tile of the group's bin of kBin^3 cells, which goes to the
+// grid at the end.  Interpolation: one block per group stages the footprint
+// values in shared memory once and evaluates every target of the group from
+// them, a thread per target.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "../../include/mbo_surface.h"
@@ -38,12 +46,11 @@
 namespace mbo {
 namespace {
 
-constexpr int kBin = 8;          // spreading / interpolation bin: kBin^3 grid cells
-constexpr int kMaxWidth = 12;    // kernel width limit (FP64)
-constexpr int kMaxWidthF32 = 8;  // FP32: single precision holds no more digits
-constexpr int kSpreadThreads = 256;
-constexpr int kInterpThreads = 256;
-constexpr size_t kTileBudget = 76 * 1024;  // shared bytes of one spreading tile
+constexpr int kBin = 8;         // spreading bin: kBin^3 grid cells
+constexpr int kMaxW = 8;        // kernel width limit (register arrays)
+constexpr int kMinW = 4;
+constexpr int kSpreadThreads = 512;
+constexpr int kProjThreads = 256;
 
 template <typename T> struct V4 { T x, y, z, w; };
 
@@ -57,70 +64,119 @@ template <typename T> __device__ __forceinline__ T es_kernel(T z, T beta) {
   return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
 }
 
-// First footprint index of a coordinate o (offset from the bin origin, grid
-// units) relative to the tile origin (bin origin - W/2), clamped so that the
-// W points stay inside the tile whatever the rounding of o.
-template <typename T> __device__ __forceinline__ int foot0(T o, int W) {
-  int t = (int)ceil(o - T(0.5) * T(W)) + W / 2;
-  return min(max(t, 0), kBin);
+// Lane l < 3W of a warp computes the 1-D weight of footprint point l % W along
+// axis l / W for a point at distance d (grid units, per axis) past the
+// footprint's first point: phi(2 (i - d) / W).
+template <typename T>
+__device__ __forceinline__ T lane_weight(int lane, int W, T dx, T dy, T dz, T beta) {
+  if (lane >= 3 * W) return T(0);
+  const int ax = lane / W, i = lane - ax * W;
+  const T d = ax == 0 ? dx : (ax == 1 ? dy : dz);
+  return es_kernel((T(i) - d) * (T(2) / T(W)), beta);
 }
 
 template <typename T> struct SpreadArgs {
   const T* A;            // surface field, C x nq
-  const V4<T>* su;       // sources sorted by bin: offsets from the bin origin, weight
+  const V4<T>* su;       // sources sorted by (bin, group): d per axis, weight w_q
   const int* sidx;       // source -> field point
-  const int* bstart;     // per non-empty bin: first source (nbins + 1 entries)
-  const int* bid;        // per non-empty bin: bin id (bz nb + by) nb + bx
+  const int* gsrc;       // group -> first source (ngroups + 1)
+  const int* gt0;        // group -> footprint start in the bin tile, t0x | t0y << 4 | t0z << 8
+  const int* bgrp;       // bin -> first group (nbins + 1)
+  const int* bid;        // bin -> bin id (bz nb + by) nb + bx
   T* F;                  // grid, C x nf^3
   long long nq;
   int C, nf, nb, W;
   T beta;
 };
 
-// One block per (non-empty bin, group of CG channels).
+// One block per (non-empty bin, group of CG channels); one warp per point
+// group.  A group holds the sources of a bin whose footprints start at the
+// same z and within a 2 x 2 block in (x, y), so its footprint is
+// (W + 1) x (W + 1) x W points (a source's weights vanish outside its own W^3).
+// The warp stages up to chunk_of<T>() sources at a time in shared memory
+// (their one-dimensional weights on the group footprint and CG strengths
+// w_q A), then each lane sums one footprint column (x, y) over them, W points
+// along z in registers, and adds the column to the bin tile.
+template <typename T> __host__ __device__ constexpr int chunk_of() { return sizeof(T) == 4 ? 32 : 16; }
+constexpr int kWS = kMaxW + 1;  // weight slots per axis
 template <typename T, int CG>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
-  const int W = a.W, TS = kBin + W, TV = TS * TS * TS;
+  const int W = a.W, FW = W + 1, TX = kBin + FW, TZ = kBin + W, TV = TX * TX * TZ;
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [c][z][y][x], TX x TX x TZ
   const int c0 = blockIdx.y * CG;
   const int cg = min(CG, a.C - c0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // per warp: weights [CH][3 kWS] and strengths [CH][CG]
+  constexpr int CH = chunk_of<T>();
+  T* wts = tile + CG * TV + warp * CH * (3 * kWS + CG);
+  T* sts = wts + CH * 3 * kWS;
   for (int i = tid; i < CG * TV; i += kSpreadThreads) tile[i] = T(0);
   __syncthreads();
 
-  const int s0 = a.bstart[blockIdx.x], s1 = a.bstart[blockIdx.x + 1];
-  const int W2 = W * W, W3 = W2 * W, iters = (W3 + 31) >> 5;
-  for (int s = s0 + warp; s < s1; s += kSpreadThreads / 32) {
-    const V4<T> u = a.su[s];
-    const long long src = a.sidx[s];
-    const int tx = foot0(u.x, W), ty = foot0(u.y, W), tz = foot0(u.z, W);
-    // lane l < 3W: the 1-D weight of point l % W along axis l / W
-    T wt = T(0);
-    if (lane < 3 * W) {
-      const int ax = lane / W, i = lane - ax * W;
-      const T o = ax == 0 ? u.x : (ax == 1 ? u.y : u.z);
-      const int t0 = ax == 0 ? tx : (ax == 1 ? ty : tz);
-      const T z = (T(t0 + i - W / 2) - o) * (T(2) / T(W));
-      wt = es_kernel(z, a.beta);
-    }
-    T str[CG];
+  const int F2 = FW * FW;
+  const T sc2 = T(2) / T(W);
+  const int g0 = a.bgrp[blockIdx.x], g1 = a.bgrp[blockIdx.x + 1];
+  for (int g = g0 + warp; g < g1; g += kSpreadThreads / 32) {
+    const int pk = a.gt0[g];
+    const int tx = pk & 15, ty = (pk >> 4) & 15, tz = (pk >> 8) & 15;
+    const int s0 = a.gsrc[g], s1 = a.gsrc[g + 1];
+    for (int cs = s0; cs < s1; cs += CH) {
+      const int ns = min(CH, s1 - cs);
+      __syncwarp();
+      if (lane < ns) {
+        const V4<T> u = a.su[cs + lane];  // distance past the group footprint start
+        const long long src = a.sidx[cs + lane];
+        T* w = wts + lane * 3 * kWS;
 #pragma unroll
-    for (int c = 0; c < CG; ++c) str[c] = (c < cg) ? a.A[(long long)(c0 + c) * a.nq + src] * u.w : T(0);
-    for (int it = 0; it < iters; ++it) {
-      const int p = lane + 32 * it;
-      const bool ok = p < W3;
-      const int pp = ok ? p : 0;
-      const int k = pp / W2, r = pp - k * W2, j = r / W, i = r - j * W;
-      const T wx = __shfl_sync(0xffffffffu, wt, i);
-      const T wy = __shfl_sync(0xffffffffu, wt, W + j);
-      const T wz = __shfl_sync(0xffffffffu, wt, 2 * W + k);
-      if (ok) {
-        const T wgt = wx * wy * wz;
-        const int addr = ((tz + k) * TS + ty + j) * TS + tx + i;
+        for (int i = 0; i < kWS; ++i) {
+          if (i < FW) {
+            w[i] = es_kernel((T(i) - u.x) * sc2, a.beta);
+            w[kWS + i] = es_kernel((T(i) - u.y) * sc2, a.beta);
+          }
+          if (i < W) w[2 * kWS + i] = es_kernel((T(i) - u.z) * sc2, a.beta);
+        }
 #pragma unroll
         for (int c = 0; c < CG; ++c)
-          if (c < cg) atomicAdd(&tile[c * TV + addr], wgt * str[c]);
+          sts[lane * CG + c] = (c < cg) ? a.A[(long long)(c0 + c) * a.nq + src] * u.w : T(0);
+      }
+      __syncwarp();
+      for (int rd = 0; rd * 32 < F2; ++rd) {
+        const int p = lane + 32 * rd;
+        const bool ok = p < F2;
+        const int j = ok ? p / FW : 0, i = ok ? p - j * FW : 0;
+        T acc[kMaxW][CG];
+#pragma unroll
+        for (int k = 0; k < kMaxW; ++k)
+#pragma unroll
+          for (int c = 0; c < CG; ++c) acc[k][c] = T(0);
+        for (int q = 0; q < ns; ++q) {
+          const T* wq = wts + q * 3 * kWS;
+          const T wxy = wq[i] * wq[kWS + j];
+          T str[CG];
+#pragma unroll
+          for (int c = 0; c < CG; ++c) str[c] = sts[q * CG + c] * wxy;
+#pragma unroll
+          for (int k = 0; k < kMaxW; ++k) {
+            if (k < W) {
+              const T wz = wq[2 * kWS + k];
+#pragma unroll
+              for (int c = 0; c < CG; ++c) acc[k][c] += wz * str[c];
+            }
+          }
+        }
+        if (ok) {
+          int addr = (tz * TX + ty + j) * TX + tx + i;
+#pragma unroll
+          for (int k = 0; k < kMaxW; ++k) {
+            if (k < W) {
+#pragma unroll
+              for (int c = 0; c < CG; ++c)
+                if (c < cg) atomicAdd(&tile[c * TV + addr], acc[k][c]);
+            }
+            addr += TX * TX;
+          }
+        }
       }
     }
   }
@@ -137,7 +193,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
     for (int i = tid; i < TV; i += kSpreadThreads) {
       const T v = tile[c * TV + i];
       if (v == T(0)) continue;
-      const int x = i % TS, y = (i / TS) % TS, z = i / (TS * TS);
+      const int x = i % TX, y = (i / TX) % TX, z = i / (TX * TX);
       const int gx = (lx + x) % nf, gy = (ly + y) % nf, gz = (lz + z) % nf;
       atomicAdd(&Fc[((long long)gz * nf + gy) * nf + gx], v);
     }
@@ -146,117 +202,155 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
 
 template <typename T> struct InterpArgs {
   const T* F;          // grid, C x nf^3
-  const V4<T>* tu;     // targets sorted by bin: offsets from the bin origin
-  const int* tbin;     // target bin id
+  const V4<T>* tu;     // targets sorted by group: d per axis
   const int* tidx;     // target -> field point
-  T* out;              // C x nq: diffused field (diffuse) or the field itself (step)
-  SurfStats* st;       // step statistics (step only)
+  const int* tgrp;     // group -> first target (ngroups + 1)
+  const int4* tg0;     // group -> first footprint point on the grid (gx, gy, gz)
+  T* dst;              // C x nq: out[c][tidx[t]] (diffuse) or scratch[c][t] (step)
   long long nq;
-  int nf, nb, W;
-  T beta, fb;
+  int nf, W;
+  bool scatter;        // write at tidx[t] (true) or at t (false)
+  T beta;
 };
 
-// One warp per group of 32 sorted targets: for each target the lanes sum the
-// W^3 grid points (lane-parallel) and reduce; then lane l finishes target l.
-template <typename T, int NM, bool STEP>
-__global__ void __launch_bounds__(kInterpThreads) k_interp(InterpArgs<T> a) {
-  constexpr int C = NM * NM;
-  __shared__ T res[kInterpThreads / 32][32][C];
-  __shared__ double redd[32];
-  __shared__ int redi[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long long base = ((long long)blockIdx.x * (kInterpThreads / 32) + warp) * 32;
-  const int W = a.W, W2 = W * W, W3 = W2 * W, iters = (W3 + 31) >> 5;
-  const int nf = a.nf;
+// One block per target group: the group's W^3 footprint values (C channels
+// padded to CP, point-major) are staged in shared memory once; each thread
+// evaluates one target from them (all lanes of a warp read the same values:
+// broadcast), with its 3W one-dimensional weights in registers.
+constexpr int kInterpBlock = 128;
+template <typename T, int C> __host__ __device__ constexpr int padded_channels() {
+  return C == 1 ? 1 : (sizeof(T) == 4 ? (C + 3) / 4 * 4 : (C + 1) / 2 * 2);
+}
+template <typename T, int NM>
+__global__ void __launch_bounds__(kInterpBlock) k_interp(InterpArgs<T> a) {
+  constexpr int C = NM * NM, CP = padded_channels<T, C>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* fp = reinterpret_cast<T*>(smem_raw);  // [W^3][CP]
+  const int W = a.W, W2 = W * W, W3 = W2 * W, nf = a.nf;
   const long long P = (long long)nf * nf * nf;
-  for (int e = 0; e < 32; ++e) {
-    const long long t = base + e;
-    if (t >= a.nq) break;  // warp-uniform
-    const V4<T> u = a.tu[t];
-    const int b = a.tbin[t];
-    const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
-    const int tx = foot0(u.x, W), ty = foot0(u.y, W), tz = foot0(u.z, W);
-    T wt = T(0);
-    if (lane < 3 * W) {
-      const int ax = lane / W, i = lane - ax * W;
-      const T o = ax == 0 ? u.x : (ax == 1 ? u.y : u.z);
-      const int t0 = ax == 0 ? tx : (ax == 1 ? ty : tz);
-      const T z = (T(t0 + i - W / 2) - o) * (T(2) / T(W));
-      wt = es_kernel(z, a.beta);
+  const int g = blockIdx.x;
+  const int4 g0 = a.tg0[g];
+  for (int e = threadIdx.x; e < CP * W3; e += kInterpBlock) {
+    const int c = e / W3, p = e - c * W3;
+    T v = T(0);
+    if (c < C) {
+      const int k = p / W2, r = p - k * W2, j = r / W, i = r - j * W;
+      int gx = g0.x + i, gy = g0.y + j, gz = g0.z + k;
+      gx -= gx >= nf ? nf : 0;
+      gy -= gy >= nf ? nf : 0;
+      gz -= gz >= nf ? nf : 0;
+      v = __ldg(&a.F[c * P + ((long long)gz * nf + gy) * nf + gx]);
     }
-    const int lx = bx * kBin - W / 2 + tx + nf, ly = by * kBin - W / 2 + ty + nf,
-              lz = bz * kBin - W / 2 + tz + nf;
-    T acc[C];
+    fp[p * CP + c] = v;
+  }
+  __syncthreads();
+  const int t1 = a.tgrp[g + 1];
+  const T sc2 = T(2) / T(W);
+  for (int t = a.tgrp[g] + threadIdx.x; t < t1; t += kInterpBlock) {
+    const V4<T> u = a.tu[t];
+    T wx[kMaxW], wy[kMaxW];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = T(0);
-    for (int it = 0; it < iters; ++it) {
-      const int p = lane + 32 * it;
-      const bool ok = p < W3;
-      const int pp = ok ? p : 0;
-      const int k = pp / W2, r = pp - k * W2, j = r / W, i = r - j * W;
-      const T wx = __shfl_sync(0xffffffffu, wt, i);
-      const T wy = __shfl_sync(0xffffffffu, wt, W + j);
-      const T wz = __shfl_sync(0xffffffffu, wt, 2 * W + k);
-      if (ok) {
-        const T wgt = wx * wy * wz;
-        const long long o = ((long long)((lz + k) % nf) * nf + (ly + j) % nf) * nf + (lx + i) % nf;
+    for (int i = 0; i < kMaxW; ++i) {
+      wx[i] = (i < W) ? es_kernel((T(i) - u.x) * sc2, a.beta) : T(0);
+      wy[i] = (i < W) ? es_kernel((T(i) - u.y) * sc2, a.beta) : T(0);
+    }
+    T acc[CP];
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] += wgt * __ldg(&a.F[c * P + o]);
+    for (int c = 0; c < CP; ++c) acc[c] = T(0);
+    for (int k = 0; k < W; ++k) {
+      const T wz = es_kernel((T(k) - u.z) * sc2, a.beta);
+      const T* plane = fp + k * W2 * CP;
+#pragma unroll
+      for (int j = 0; j < kMaxW; ++j) {
+        if (j < W) {
+          const T wyz = wz * wy[j];
+#pragma unroll
+          for (int i = 0; i < kMaxW; ++i) {
+            if (i < W) {
+              const T w = wyz * wx[i];
+              const T* pt = plane + (j * W + i) * CP;
+              if constexpr (CP % 4 == 0 && sizeof(T) == 4) {
+#pragma unroll
+                for (int v = 0; v < CP / 4; ++v) {
+                  const float4 x = reinterpret_cast<const float4*>(pt)[v];
+                  acc[4 * v] += w * x.x;
+                  acc[4 * v + 1] += w * x.y;
+                  acc[4 * v + 2] += w * x.z;
+                  acc[4 * v + 3] += w * x.w;
+                }
+              } else if constexpr (CP % 2 == 0 && sizeof(T) == 8) {
+#pragma unroll
+                for (int v = 0; v < CP / 2; ++v) {
+                  const double2 x = reinterpret_cast<const double2*>(pt)[v];
+                  acc[2 * v] += w * x.x;
+                  acc[2 * v + 1] += w * x.y;
+                }
+              } else {
+#pragma unroll
+                for (int c = 0; c < CP; ++c) acc[c] += w * pt[c];
+              }
+            }
+          }
+        }
       }
     }
+    const long long q = a.scatter ? (long long)a.tidx[t] : (long long)t;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      T v = acc[c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) res[warp][e][c] = v;
-    }
+    for (int c = 0; c < C; ++c) a.dst[c * a.nq + q] = acc[c];
   }
-  __syncwarp();
+}
 
-  const long long t = base + lane;
+template <typename T> struct ProjArgs {
+  const T* At;        // C x nq diffused values, sorted target order
+  const int* tidx;    // target -> field point
+  T* A;               // field, C x nq (read: previous; written: projected)
+  SurfStats* st;
+  long long nq;
+  T fb;
+};
+
+// Projection of every target (Lemma 1.1) and the step statistics.
+template <typename T, int NM>
+__global__ void __launch_bounds__(kProjThreads) k_sproject(ProjArgs<T> a) {
+  constexpr int C = NM * NM;
+  __shared__ double redd[32];
+  __shared__ int redi[32];
+  const long long t = (long long)blockIdx.x * kProjThreads + threadIdx.x;
   PointStats<T> ps;
   if (t < a.nq) {
     const long long q = a.tidx[t];
-    T m[C];
+    T m[C], old[C], bb[C], sg;
 #pragma unroll
-    for (int c = 0; c < C; ++c) m[c] = res[warp][lane][c];
-    if constexpr (!STEP) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) a.out[c * a.nq + q] = m[c];
-    } else {
-      T old[C], bb[C], sg;
-#pragma unroll
-      for (int c = 0; c < C; ++c) old[c] = a.out[c * a.nq + q];
-      bool fin = true;
-#pragma unroll
-      for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
-      ps.nonfinite += fin ? 0 : 1;
-      if (!project_point<NM>(m, bb, sg, a.fb)) {
-        sg = project_point_f64<NM>(m, bb);
-        ps.fallback += 1;
-      }
-      T d = T(0);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        d = fmax(d, fabs(bb[c] - old[c]));
-        a.out[c * a.nq + q] = bb[c];
-      }
-      ps.maxd = fmax(ps.maxd, d);
-      ps.flips += (det_sign<NM>(old) != sg) ? 1 : 0;
+    for (int c = 0; c < C; ++c) {
+      m[c] = a.At[c * a.nq + t];
+      old[c] = a.A[c * a.nq + q];
     }
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+    ps.nonfinite += fin ? 0 : 1;
+    if (!project_point<NM>(m, bb, sg, a.fb)) {
+      sg = project_point_f64<NM>(m, bb);
+      ps.fallback += 1;
+    }
+    T d = T(0);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      d = fmax(d, fabs(bb[c] - old[c]));
+      a.A[c * a.nq + q] = bb[c];
+    }
+    ps.maxd = d;
+    ps.flips = (det_sign<NM>(old) != sg) ? 1 : 0;
   }
-  if constexpr (STEP) {
-    const double mx = block_max((double)ps.maxd, redd);
-    const int fl = block_sum(ps.flips, redi);
-    const int nfin = block_sum(ps.nonfinite, redi);
-    const int nfb = block_sum(ps.fallback, redi);
-    if (tid == 0) {
-      atomicMax(&a.st->maxd_bits, (unsigned long long)__double_as_longlong(mx));
-      if (fl) atomicAdd(&a.st->flips, (unsigned long long)fl);
-      if (nfin) atomicAdd(&a.st->nonfinite, (unsigned long long)nfin);
-      if (nfb) atomicAdd(&a.st->fallback, (unsigned long long)nfb);
-    }
+  const double mx = block_max((double)ps.maxd, redd);
+  const int fl = block_sum(ps.flips, redi);
+  const int nfin = block_sum(ps.nonfinite, redi);
+  const int nfb = block_sum(ps.fallback, redi);
+  if (threadIdx.x == 0) {
+    atomicMax(&a.st->maxd_bits, (unsigned long long)__double_as_longlong(mx));
+    if (fl) atomicAdd(&a.st->flips, (unsigned long long)fl);
+    if (nfin) atomicAdd(&a.st->nonfinite, (unsigned long long)nfin);
+    if (nfb) atomicAdd(&a.st->fallback, (unsigned long long)nfb);
   }
 }
 
@@ -310,19 +404,25 @@ struct mbo_surface_ctx {
   long long nq = 0;
   double tau = 0, eps = 0;
   mbo_surface_params prm{};
-  int nb = 0;  // bins per axis
-  int nbins = 0;  // non-empty source bins
-  int cg = 1, ngroups = 1;
+  int nb = 0;        // bins per axis
+  int nbins = 0;     // non-empty source bins
+  int sgroups = 0;   // source groups
+  int tgroups = 0;   // target groups
+  int cg = 1, chgroups = 1;  // channels per spreading block, channel groups
   size_t tile_bytes = 0;
   mbo_handle fine = nullptr;  // 3-D FFT diffusion on the nf^3 grid
   void* F = nullptr;          // grid, C x nf^3
+  void* At = nullptr;         // diffused values in sorted target order, C x nq
   void* su = nullptr;         // V4<T> sources
   int* sidx = nullptr;
-  int* bstart = nullptr;
+  int* gsrc = nullptr;
+  int* gt0 = nullptr;
+  int* bgrp = nullptr;
   int* bid = nullptr;
   void* tu = nullptr;         // V4<T> targets
-  int* tbin = nullptr;
   int* tidx = nullptr;
+  int* tgrp = nullptr;
+  int4* tg0 = nullptr;
   SurfStats* st = nullptr;
   SurfStats* h_st = nullptr;  // pinned
   size_t bytes = 0;
@@ -344,8 +444,21 @@ mbo_status sfail(mbo_surface_ctx* s, mbo_status rc, const char* fmt, const char*
                    "%s", cudaGetErrorString(e_));                                           \
   } while (0)
 
-template <typename T, int CG> cudaError_t spread_cg(const SpreadArgs<T>& a, dim3 grid, size_t smem,
-                                                    cudaStream_t st) {
+// Channels per spreading block for n*n channels: the largest instantiated
+// group whose tile and staging fit in `limit` shared bytes (0 if none fits).
+int spread_cg(int C, size_t elem, size_t tv, size_t limit) {
+  const int cand[] = {9, 8, 4, 3, 1};
+  const size_t chunk = elem == 4 ? chunk_of<float>() : chunk_of<double>();
+  for (int cg : cand) {
+    if (cg > C || (elem == 8 && cg > 4)) continue;  // FP64: at most 4 (registers)
+    const size_t b = ((size_t)cg * tv + (size_t)(kSpreadThreads / 32) * chunk * (3 * kWS + cg)) * elem;
+    if (b <= limit) return cg;
+  }
+  return 0;
+}
+
+template <typename T, int CG> cudaError_t spread_run(const SpreadArgs<T>& a, dim3 grid, size_t smem,
+                                                     cudaStream_t st) {
   auto k = k_spread<T, CG>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -360,7 +473,9 @@ template <typename T> cudaError_t launch_spread(mbo_surface_ctx* s, const void* 
   a.A = static_cast<const T*>(A);
   a.su = static_cast<const V4<T>*>(s->su);
   a.sidx = s->sidx;
-  a.bstart = s->bstart;
+  a.gsrc = s->gsrc;
+  a.gt0 = s->gt0;
+  a.bgrp = s->bgrp;
   a.bid = s->bid;
   a.F = static_cast<T*>(s->F);
   a.nq = s->nq;
@@ -369,54 +484,83 @@ template <typename T> cudaError_t launch_spread(mbo_surface_ctx* s, const void* 
   a.nb = s->nb;
   a.W = s->prm.width;
   a.beta = (T)s->prm.beta;
-  const dim3 grid(s->nbins, s->ngroups);
+  const dim3 grid(s->nbins, s->chgroups);
   switch (s->cg) {
-    case 1: return spread_cg<T, 1>(a, grid, s->tile_bytes, st);
-    case 2: return spread_cg<T, 2>(a, grid, s->tile_bytes, st);
-    case 3: return spread_cg<T, 3>(a, grid, s->tile_bytes, st);
-    case 4: return spread_cg<T, 4>(a, grid, s->tile_bytes, st);
-    case 5: return spread_cg<T, 5>(a, grid, s->tile_bytes, st);
+    case 1: return spread_run<T, 1>(a, grid, s->tile_bytes, st);
+    case 3: return spread_run<T, 3>(a, grid, s->tile_bytes, st);
+    case 4: return spread_run<T, 4>(a, grid, s->tile_bytes, st);
+    case 8: return spread_run<T, 8>(a, grid, s->tile_bytes, st);
+    case 9: return spread_run<T, 9>(a, grid, s->tile_bytes, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, bool STEP>
-cudaError_t launch_interp(mbo_surface_ctx* s, void* out, cudaStream_t st) {
+template <typename T, int NM> cudaError_t interp_run(const InterpArgs<T>& a, int groups, size_t smem,
+                                                      cudaStream_t st) {
+  auto k = k_interp<T, NM>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<groups, kInterpBlock, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_interp(mbo_surface_ctx* s, void* dst, bool scatter, cudaStream_t st) {
   InterpArgs<T> a;
   a.F = static_cast<const T*>(s->F);
   a.tu = static_cast<const V4<T>*>(s->tu);
-  a.tbin = s->tbin;
   a.tidx = s->tidx;
-  a.out = static_cast<T*>(out);
-  a.st = s->st;
+  a.tgrp = s->tgrp;
+  a.tg0 = s->tg0;
+  a.dst = static_cast<T*>(dst);
   a.nq = s->nq;
   a.nf = s->prm.nf;
-  a.nb = s->nb;
   a.W = s->prm.width;
+  a.scatter = scatter;
   a.beta = (T)s->prm.beta;
-  a.fb = T(0);
-  const long long per = (kInterpThreads / 32) * 32;
-  const unsigned blocks = (unsigned)((s->nq + per - 1) / per);
+  const int W3 = s->prm.width * s->prm.width * s->prm.width;
+  const int CP = s->C == 1 ? 1 : (sizeof(T) == 4 ? (s->C + 3) / 4 * 4 : (s->C + 1) / 2 * 2);
+  const size_t smem = (size_t)W3 * CP * sizeof(T);
   switch (s->n) {
-    case 1: k_interp<T, 1, STEP><<<blocks, kInterpThreads, 0, st>>>(a); break;
-    case 2: k_interp<T, 2, STEP><<<blocks, kInterpThreads, 0, st>>>(a); break;
-    case 3: k_interp<T, 3, STEP><<<blocks, kInterpThreads, 0, st>>>(a); break;
-    default: k_interp<T, 4, STEP><<<blocks, kInterpThreads, 0, st>>>(a); break;
+    case 1: return interp_run<T, 1>(a, s->tgroups, smem, st);
+    case 2: return interp_run<T, 2>(a, s->tgroups, smem, st);
+    case 3: return interp_run<T, 3>(a, s->tgroups, smem, st);
+    default: return interp_run<T, 4>(a, s->tgroups, smem, st);
+  }
+}
+
+template <typename T> cudaError_t launch_project(mbo_surface_ctx* s, void* A, cudaStream_t st) {
+  ProjArgs<T> a;
+  a.At = static_cast<const T*>(s->At);
+  a.tidx = s->tidx;
+  a.A = static_cast<T*>(A);
+  a.st = s->st;
+  a.nq = s->nq;
+  a.fb = T(0);
+  const unsigned blocks = (unsigned)((s->nq + kProjThreads - 1) / kProjThreads);
+  switch (s->n) {
+    case 1: k_sproject<T, 1><<<blocks, kProjThreads, 0, st>>>(a); break;
+    case 2: k_sproject<T, 2><<<blocks, kProjThreads, 0, st>>>(a); break;
+    case 3: k_sproject<T, 3><<<blocks, kProjThreads, 0, st>>>(a); break;
+    default: k_sproject<T, 4><<<blocks, kProjThreads, 0, st>>>(a); break;
   }
   return cudaGetLastError();
 }
 
-mbo_status surface_diffusion(mbo_surface_ctx* s, const void* A, cudaStream_t st) {
+mbo_status surface_diffusion(mbo_surface_ctx* s, const void* A, void* dst, bool scatter, cudaStream_t st) {
   const long long P = (long long)s->prm.nf * s->prm.nf * s->prm.nf;
   const size_t elem = s->dtype == MBO_F32 ? 4 : 8;
   SCK(cudaMemsetAsync(s->F, 0, (size_t)s->C * P * elem, st));
-  SCK(s->dtype == MBO_F32 ? launch_spread<float>(s, A, st) : launch_spread<double>(s, A, st));
+  SCK((s->dtype == MBO_F32 ? launch_spread<float>(s, A, st) : launch_spread<double>(s, A, st)));
   const mbo_status rc = mbo_diffuse(s->fine, s->F, s->F, st);
   if (rc != MBO_OK) return sfail(s, rc, "grid diffusion: %s", mbo_last_error(s->fine));
+  SCK((s->dtype == MBO_F32 ? launch_interp<float>(s, dst, scatter, st)
+                           : launch_interp<double>(s, dst, scatter, st)));
   return MBO_OK;
 }
 
-template <typename T> void pack_points(const std::vector<V4<double>>& in, void* dst) {
+template <typename T> void upload_points(const std::vector<V4<double>>& in, void* dst) {
   std::vector<V4<T>> v(in.size());
   for (size_t i = 0; i < in.size(); ++i) v[i] = V4<T>{(T)in[i].x, (T)in[i].y, (T)in[i].z, (T)in[i].w};
   cudaMemcpy(dst, v.data(), v.size() * sizeof(V4<T>), cudaMemcpyHostToDevice);
@@ -510,7 +654,8 @@ mbo_status mbo_surface_destroy(mbo_surface s) {
   else prev = -1;
   cudaDeviceSynchronize();
   if (s->fine) mbo_destroy(s->fine);
-  void* bufs[] = {s->F, s->su, s->sidx, s->bstart, s->bid, s->tu, s->tbin, s->tidx, s->st};
+  void* bufs[] = {s->F, s->At, s->su, s->sidx, s->gsrc, s->gt0, s->bgrp, s->bid,
+                  s->tu, s->tidx, s->tgrp, s->tg0, s->st};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->h_st) cudaFreeHost(s->h_st);
@@ -557,7 +702,7 @@ mbo_status mbo_surface_create(mbo_surface* out, int64_t nq, const double* xq, co
   if (!(prm.R > 0)) prm.R = 1.0;  // a single point: any radius
   mbo_surface_heat_modes(eps, tau, prm.R, &prm.h, &prm.M);
   int W = (int)std::ceil(std::log10(1.0 / eps)) + 1;
-  W = std::max(2, std::min(W, dtype == MBO_F32 ? kMaxWidthF32 : kMaxWidth));
+  W = std::max(kMinW, std::min(W, kMaxW));
   prm.width = W;
   prm.beta = 2.30 * W;
   int nf = std::max(std::max(4 * prm.M, 2 * W), 8);
@@ -570,75 +715,88 @@ mbo_status mbo_surface_create(mbo_surface* out, int64_t nq, const double* xq, co
   const int nb = (nf + kBin - 1) / kBin;
   s->nb = nb;
 
-  // grid coordinates u = (h (x - centre) + pi) nf / (2 pi), binned
+  // grid coordinates u = (h (x - centre) + pi) nf / (2 pi); the footprint of a
+  // point starts at g = ceil(u - W/2) on each axis (W points), and d = u - g
   const double sc = (double)nf / (2.0 * M_PI);
   auto grid_coord = [&](const double* x, double* u) {
     for (int a = 0; a < 3; ++a) {
-      double v = (prm.h * (x[a] - prm.center[a]) + M_PI) * sc;
+      const double v = (prm.h * (x[a] - prm.center[a]) + M_PI) * sc;
       u[a] = std::min(std::max(v, 0.0), std::nextafter((double)nf, 0.0));
     }
   };
-  auto bin_of = [&](const double* u, double* o) {
-    int b[3];
+  // sources: key (bin, footprint start in the bin tile); targets: footprint start
+  std::vector<long long> skey(nq), tkey(nq);
+  std::vector<V4<double>> sd(nq), td(nq);
+  std::vector<int> sgx(3 * nq);
+  for (int64_t i = 0; i < nq; ++i) {
+    double u[3];
+    int b[3], t0[3], g[3];
+    grid_coord(xq + 3 * i, u);
     for (int a = 0; a < 3; ++a) {
       b[a] = std::min((int)(u[a] / kBin), nb - 1);
-      o[a] = u[a] - (double)b[a] * kBin;
+      // footprint start relative to the tile origin b kBin - W/2, kept in [0, kBin];
+      // the group start rounds it down to even in x and y
+      t0[a] = (int)std::ceil(u[a] - 0.5 * W) - (b[a] * kBin - W / 2);
+      t0[a] = std::min(std::max(t0[a], 0), kBin);
+      if (a < 2) t0[a] &= ~1;
+      g[a] = b[a] * kBin - W / 2 + t0[a];
     }
-    return (b[2] * nb + b[1]) * nb + b[0];
-  };
-  const int nbin_all = nb * nb * nb;
-  std::vector<int> sb(nq), tb(nq);
-  std::vector<V4<double>> so(nq), to(nq);
-  for (int64_t i = 0; i < nq; ++i) {
-    double u[3], o[3];
-    grid_coord(xq + 3 * i, u);
-    sb[i] = bin_of(u, o);
-    so[i] = V4<double>{o[0], o[1], o[2], wq[i]};
+    const long long bin = ((long long)b[2] * nb + b[1]) * nb + b[0];
+    skey[i] = bin * 4096 + (t0[2] << 8 | t0[1] << 4 | t0[0]);
+    sd[i] = V4<double>{u[0] - g[0], u[1] - g[1], u[2] - g[2], wq[i]};
     grid_coord(xc + 3 * i, u);
-    tb[i] = bin_of(u, o);
-    to[i] = V4<double>{o[0], o[1], o[2], 0.0};
+    for (int a = 0; a < 3; ++a) g[a] = (int)std::ceil(u[a] - 0.5 * W);
+    // wrapped start on the periodic grid (u >= 0, so g >= -W/2)
+    const int gx = (g[0] + nf) % nf, gy = (g[1] + nf) % nf, gz = (g[2] + nf) % nf;
+    tkey[i] = ((long long)gz * nf + gy) * nf + gx;
+    td[i] = V4<double>{u[0] - g[0], u[1] - g[1], u[2] - g[2], 0.0};
   }
-  // counting sorts by bin (stable: original order within a bin)
-  auto sort_by = [&](const std::vector<int>& key, std::vector<int>& perm, std::vector<int>& cnt) {
-    cnt.assign(nbin_all + 1, 0);
-    for (int64_t i = 0; i < nq; ++i) ++cnt[key[i] + 1];
-    for (int b = 0; b < nbin_all; ++b) cnt[b + 1] += cnt[b];
-    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    perm.assign(nq, 0);
-    for (int64_t i = 0; i < nq; ++i) perm[pos[key[i]]++] = (int)i;
-  };
-  std::vector<int> sperm, scnt, tperm, tcnt;
-  sort_by(sb, sperm, scnt);
-  sort_by(tb, tperm, tcnt);
-  std::vector<int> bstart, bid;
-  for (int b = 0; b < nbin_all; ++b)
-    if (scnt[b + 1] > scnt[b]) {
-      bid.push_back(b);
-      bstart.push_back(scnt[b]);
+  std::vector<int> sperm(nq), tperm(nq);
+  std::iota(sperm.begin(), sperm.end(), 0);
+  std::iota(tperm.begin(), tperm.end(), 0);
+  std::stable_sort(sperm.begin(), sperm.end(), [&](int x, int y) { return skey[x] < skey[y]; });
+  std::stable_sort(tperm.begin(), tperm.end(), [&](int x, int y) { return tkey[x] < tkey[y]; });
+  std::vector<int> gsrc, gt0, bgrp, bid, tgrp;
+  std::vector<int4> tg0;
+  std::vector<V4<double>> sds(nq), tds(nq);
+  for (int64_t r = 0; r < nq; ++r) {
+    const int i = sperm[r];
+    sds[r] = sd[i];
+    if (r == 0 || skey[i] != skey[sperm[r - 1]]) {
+      const long long bin = skey[i] / 4096;
+      if (r == 0 || bin != skey[sperm[r - 1]] / 4096) {
+        bid.push_back((int)bin);
+        bgrp.push_back((int)gsrc.size());
+      }
+      gsrc.push_back((int)r);
+      gt0.push_back((int)(skey[i] % 4096));
     }
-  bstart.push_back((int)nq);
-  s->nbins = (int)bid.size();
-  prm.bins = s->nbins;
-  std::vector<V4<double>> sos(nq), tos(nq);
-  std::vector<int> tbs(nq);
-  for (int64_t i = 0; i < nq; ++i) {
-    sos[i] = so[sperm[i]];
-    tos[i] = to[tperm[i]];
-    tbs[i] = tb[tperm[i]];
+    const int j = tperm[r];
+    tds[r] = td[j];
+    if (r == 0 || tkey[j] != tkey[tperm[r - 1]]) {
+      tgrp.push_back((int)r);
+      const long long k = tkey[j];
+      tg0.push_back(make_int4((int)(k % nf), (int)((k / nf) % nf), (int)(k / ((long long)nf * nf)), 0));
+    }
   }
+  gsrc.push_back((int)nq);
+  tgrp.push_back((int)nq);
+  bgrp.push_back((int)gt0.size());
+  s->nbins = (int)bid.size();
+  s->sgroups = (int)gt0.size();
+  s->tgroups = (int)tg0.size();
+  prm.bins = s->nbins;
 
   // channel groups of the spreading tile
   const size_t elem = dtype == MBO_F32 ? 4 : 8;
-  const size_t tv = (size_t)(kBin + W) * (kBin + W) * (kBin + W);
-  const size_t per_ch = tv * elem;
-  int fit = (int)std::max<size_t>(1, kTileBudget / per_ch);
-  fit = std::min(fit, 5);
-  s->ngroups = (s->C + fit - 1) / fit;
-  s->cg = (s->C + s->ngroups - 1) / s->ngroups;
-  s->tile_bytes = (size_t)s->cg * per_ch;
+  const size_t tv = (size_t)(kBin + W + 1) * (kBin + W + 1) * (kBin + W);
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev);
-  if (s->tile_bytes > (size_t)maxsm) {
+  s->cg = spread_cg(s->C, elem, tv, (size_t)maxsm);
+  s->chgroups = s->cg ? (s->C + s->cg - 1) / s->cg : 0;
+  const size_t chunk = elem == 4 ? chunk_of<float>() : chunk_of<double>();
+  s->tile_bytes = ((size_t)s->cg * tv + (size_t)(kSpreadThreads / 32) * chunk * (3 * kWS + s->cg)) * elem;
+  if (s->cg == 0) {
     mbo_surface_destroy(s);
     return MBO_ERR_UNSUPPORTED_SIZE;
   }
@@ -680,32 +838,37 @@ mbo_status mbo_surface_create(mbo_surface* out, int64_t nq, const double* xq, co
   // device tables
   const long long P = (long long)nf * nf * nf;
   auto alloc = [&](void** p, size_t b) {
-    if (cudaMalloc(p, b) != cudaSuccess) return false;
+    if (cudaMalloc(p, std::max<size_t>(b, 16)) != cudaSuccess) return false;
     s->bytes += b;
     return true;
   };
   const size_t v4 = dtype == MBO_F32 ? sizeof(V4<float>) : sizeof(V4<double>);
-  if (!alloc(&s->F, (size_t)s->C * P * elem) || !alloc(&s->su, nq * v4) ||
-      !alloc((void**)&s->sidx, nq * sizeof(int)) || !alloc((void**)&s->bstart, bstart.size() * sizeof(int)) ||
-      !alloc((void**)&s->bid, std::max<size_t>(bid.size(), 1) * sizeof(int)) || !alloc(&s->tu, nq * v4) ||
-      !alloc((void**)&s->tbin, nq * sizeof(int)) || !alloc((void**)&s->tidx, nq * sizeof(int)) ||
+  if (!alloc(&s->F, (size_t)s->C * P * elem) || !alloc(&s->At, (size_t)s->C * nq * elem) ||
+      !alloc(&s->su, nq * v4) || !alloc((void**)&s->sidx, nq * sizeof(int)) ||
+      !alloc((void**)&s->gsrc, gsrc.size() * sizeof(int)) || !alloc((void**)&s->gt0, gt0.size() * sizeof(int)) ||
+      !alloc((void**)&s->bgrp, bgrp.size() * sizeof(int)) || !alloc((void**)&s->bid, bid.size() * sizeof(int)) ||
+      !alloc(&s->tu, nq * v4) || !alloc((void**)&s->tidx, nq * sizeof(int)) ||
+      !alloc((void**)&s->tgrp, tgrp.size() * sizeof(int)) || !alloc((void**)&s->tg0, tg0.size() * sizeof(int4)) ||
       !alloc((void**)&s->st, sizeof(SurfStats)) ||
       cudaMallocHost((void**)&s->h_st, sizeof(SurfStats)) != cudaSuccess) {
     mbo_surface_destroy(s);
     return MBO_ERR_OOM;
   }
   if (dtype == MBO_F32) {
-    pack_points<float>(sos, s->su);
-    pack_points<float>(tos, s->tu);
+    upload_points<float>(sds, s->su);
+    upload_points<float>(tds, s->tu);
   } else {
-    pack_points<double>(sos, s->su);
-    pack_points<double>(tos, s->tu);
+    upload_points<double>(sds, s->su);
+    upload_points<double>(tds, s->tu);
   }
   cudaMemcpy(s->sidx, sperm.data(), nq * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(s->bstart, bstart.data(), bstart.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (!bid.empty()) cudaMemcpy(s->bid, bid.data(), bid.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(s->tbin, tbs.data(), nq * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->gsrc, gsrc.data(), gsrc.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->gt0, gt0.data(), gt0.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->bgrp, bgrp.data(), bgrp.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->bid, bid.data(), bid.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(s->tidx, tperm.data(), nq * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->tgrp, tgrp.data(), tgrp.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->tg0, tg0.data(), tg0.size() * sizeof(int4), cudaMemcpyHostToDevice);
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     snprintf(s->err, sizeof(s->err), "table upload: %s", cudaGetErrorString(e));
@@ -724,28 +887,22 @@ mbo_status mbo_surface_get_params(mbo_surface s, mbo_surface_params* p) {
 
 mbo_status mbo_surface_diffuse(mbo_surface s, const void* A, void* A_tilde, void* stream) {
   if (!s || !A || !A_tilde || ((uintptr_t)A & 15) || ((uintptr_t)A_tilde & 15)) return MBO_ERR_INVALID_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  mbo_status rc = surface_diffusion(s, A, st);
-  if (rc != MBO_OK) return rc;
-  SCK((s->dtype == MBO_F32 ? launch_interp<float, false>(s, A_tilde, st)
-                           : launch_interp<double, false>(s, A_tilde, st)));
-  return MBO_OK;
+  return surface_diffusion(s, A, A_tilde, true, static_cast<cudaStream_t>(stream));
 }
 
 mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stream) {
   if (!s || !A || ((uintptr_t)A & 15)) return MBO_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  mbo_status rc = surface_diffusion(s, A, st);
+  mbo_status rc = surface_diffusion(s, A, s->At, false, st);
   if (rc != MBO_OK) return rc;
   SCK(cudaMemsetAsync(s->st, 0, sizeof(SurfStats), st));
-  SCK((s->dtype == MBO_F32 ? launch_interp<float, true>(s, A, st)
-                           : launch_interp<double, true>(s, A, st)));
+  SCK((s->dtype == MBO_F32 ? launch_project<float>(s, A, st) : launch_project<double>(s, A, st)));
   if (stats) {
     SCK(cudaMemcpyAsync(s->h_st, s->st, sizeof(SurfStats), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
-    stats->energy = NAN;
     double md;
     std::memcpy(&md, &s->h_st->maxd_bits, sizeof(md));
+    stats->energy = NAN;
     stats->max_delta = md;
     stats->det_flips = (int64_t)s->h_st->flips;
     stats->fallback_points = (int64_t)s->h_st->fallback;

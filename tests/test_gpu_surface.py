@@ -5,7 +5,8 @@ GPU against the oracle (oracle/surface.py).
   theorem, R the points' extent); the grid is 2^a 3^b and at least 4M.
 * Diffusion: the GPU's spreading / FFT / interpolation equals the oracle's
   plain double sum at every point, to the accuracy the spreading width buys
-  (FP32, eps = 1e-6: 2e-5 of the field's scale; FP64, eps = 1e-9: 1e-7),
+  (FP32, eps = 1e-6: 2e-5 of the field's scale; FP64, eps = 1e-7, the
+  widest kernel: 2e-6),
   for n = 1..4 on clustered random points (empty and crowded bins, a ragged
   last block) and on a coarse sphere band.
 * Step: the projected field equals the oracle's step where the class is
@@ -30,8 +31,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-TOL = {"f32": 2e-5, "f64": 1e-7}
-EPS = {"f32": 1e-6, "f64": 1e-9}
+TOL = {"f32": 2e-5, "f64": 2e-6}
+EPS = {"f32": 1e-6, "f64": 1e-7}
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +84,7 @@ def test_params_match_the_oracle(M, dtype):
     while k % 3 == 0:
         k //= 3
     assert k == 1
-    assert p["width"] == min(math.ceil(math.log10(1 / EPS[dtype])) + 1, 8 if dtype == "f32" else 12)
+    assert p["width"] == min(max(math.ceil(math.log10(1 / EPS[dtype])) + 1, 4), 8)
     assert p["bins"] > 1
     s.close()
 
@@ -124,7 +125,7 @@ def test_diffuse_and_step_match_the_oracle_on_clusters(M, n, dtype):
     s.close()
 
 
-@pytest.mark.parametrize("dtype,n,eps", [("f32", 3, 1e-6), ("f64", 2, 1e-9)])
+@pytest.mark.parametrize("dtype,n,eps", [("f32", 3, 1e-6), ("f64", 2, 1e-7)])
 def test_coarse_sphere_band(M, dtype, n, eps):
     tau = 0.05
     wb = S.band_width(eps, tau)
