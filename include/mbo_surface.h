@@ -115,6 +115,17 @@ MBO_API mbo_status mbo_surface_diffuse(mbo_surface s, const void* A, void* A_til
  * energy is NaN (the surface path defines no Lyapunov value). */
 MBO_API mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stream);
 
+/* Per-pass device timing of the surface calls (CUDA events around each
+ * launch on the caller's stream; off by default).  Passes, in this order:
+ * spreading (k_spread), the grid's FFT diffusion (all its passes together),
+ * interpolation (k_interp), projection (k_sproject).  mbo_surface_profile_enable
+ * (re)starts the accumulation; mbo_surface_profile_read synchronises on the
+ * recorded events and returns, for the first npass passes, the accumulated
+ * milliseconds and the number of timed calls. */
+enum { MBO_SURFACE_PROFILE_PASSES = 4 };
+MBO_API mbo_status mbo_surface_profile_enable(mbo_surface s, int enable);
+MBO_API mbo_status mbo_surface_profile_read(mbo_surface s, double* ms, int64_t* launches, int npass);
+
 /* Device bytes the plan holds. */
 MBO_API int64_t mbo_surface_workspace_bytes(mbo_surface s);
 

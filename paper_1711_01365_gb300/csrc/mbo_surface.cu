@@ -37,6 +37,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mbo_surface.h"
@@ -93,24 +94,30 @@ template <typename T> struct SpreadArgs {
 // group.  A group holds the sources of a bin whose footprints start at the
 // same z and within a 2 x 2 block in (x, y), so its footprint is
 // (W + 1) x (W + 1) x W points (a source's weights vanish outside its own W^3).
-// The warp stages up to chunk_of<T>() sources at a time in shared memory
-// (their one-dimensional weights on the group footprint and CG strengths
-// w_q A), then each lane sums one footprint column (x, y) over them, W points
-// along z in registers, and adds the column to the bin tile.
+// The warp stages chunk_of<T>() sources at a time in shared memory, lane l the
+// l-th source (its one-dimensional weights, z first, and strengths w_q A, in
+// 16-byte vectors; the per-source stride makes the vector stores of a quarter
+// warp hit distinct banks); then lane p of round rd owns footprint column
+// (x, y) = (p % (W+1), p / (W+1)), p = lane + 32 rd, sums it over the chunk, W
+// points along z for CG channels in registers, and adds it to the bin tile.
 template <typename T> __host__ __device__ constexpr int chunk_of() { return sizeof(T) == 4 ? 32 : 16; }
-constexpr int kWS = kMaxW + 1;  // weight slots per axis
+constexpr int kWS = 9;     // weight slots of x and of y per source (>= W + 1)
+constexpr int kWSrc = 28;  // per source: z[8] | x[kWS] | y[kWS] | 2 pad, then strengths
+template <typename T> __host__ __device__ constexpr int src_stride() { return sizeof(T) == 4 ? 44 : 34; }
 template <typename T, int CG>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CH = chunk_of<T>(), SRC = src_stride<T>();
+  constexpr int VW = 16 / sizeof(T);  // elements per 16-byte vector
+  constexpr int CGP = (CG + VW - 1) / VW * VW;
+  static_assert(kWSrc + CGP <= SRC, "strengths must fit the source stride");
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   const int W = a.W, FW = W + 1, TX = kBin + FW, TZ = kBin + W, TV = TX * TX * TZ;
   T* tile = reinterpret_cast<T*>(smem_raw);  // [c][z][y][x], TX x TX x TZ
   const int c0 = blockIdx.y * CG;
   const int cg = min(CG, a.C - c0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // per warp: weights [CH][3 kWS] and strengths [CH][CG]
-  constexpr int CH = chunk_of<T>();
-  T* wts = tile + CG * TV + warp * CH * (3 * kWS + CG);
-  T* sts = wts + CH * 3 * kWS;
+  T* stg = tile + ((CG * TV + VW - 1) / VW) * VW + warp * CH * SRC;  // 16-byte aligned
   for (int i = tid; i < CG * TV; i += kSpreadThreads) tile[i] = T(0);
   __syncthreads();
 
@@ -127,18 +134,25 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
       if (lane < ns) {
         const V4<T> u = a.su[cs + lane];  // distance past the group footprint start
         const long long src = a.sidx[cs + lane];
-        T* w = wts + lane * 3 * kWS;
+        T r[SRC];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = (k < W) ? es_kernel((T(k) - u.z) * sc2, a.beta) : T(0);
 #pragma unroll
         for (int i = 0; i < kWS; ++i) {
-          if (i < FW) {
-            w[i] = es_kernel((T(i) - u.x) * sc2, a.beta);
-            w[kWS + i] = es_kernel((T(i) - u.y) * sc2, a.beta);
-          }
-          if (i < W) w[2 * kWS + i] = es_kernel((T(i) - u.z) * sc2, a.beta);
+          r[8 + i] = (i < FW) ? es_kernel((T(i) - u.x) * sc2, a.beta) : T(0);
+          r[8 + kWS + i] = (i < FW) ? es_kernel((T(i) - u.y) * sc2, a.beta) : T(0);
         }
 #pragma unroll
-        for (int c = 0; c < CG; ++c)
-          sts[lane * CG + c] = (c < cg) ? a.A[(long long)(c0 + c) * a.nq + src] * u.w : T(0);
+        for (int e = 8 + 2 * kWS; e < kWSrc; ++e) r[e] = T(0);
+#pragma unroll
+        for (int c = 0; c < SRC - kWSrc; ++c)
+          r[kWSrc + c] = (c < cg) ? a.A[(long long)(c0 + c) * a.nq + src] * u.w : T(0);
+        V* dst = reinterpret_cast<V*>(stg + lane * SRC);
+#pragma unroll
+        for (int v = 0; v < SRC / VW; ++v) {
+          if constexpr (VW == 4) dst[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+          else dst[v] = make_double2(r[2 * v], r[2 * v + 1]);
+        }
       }
       __syncwarp();
       for (int rd = 0; rd * 32 < F2; ++rd) {
@@ -151,17 +165,29 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
 #pragma unroll
           for (int c = 0; c < CG; ++c) acc[k][c] = T(0);
         for (int q = 0; q < ns; ++q) {
-          const T* wq = wts + q * 3 * kWS;
-          const T wxy = wq[i] * wq[kWS + j];
-          T str[CG];
+          const T* wq = stg + q * SRC;
+          const T wxy = wq[8 + i] * wq[8 + kWS + j];
+          T wz[8], str[CGP];
 #pragma unroll
-          for (int c = 0; c < CG; ++c) str[c] = sts[q * CG + c] * wxy;
+          for (int v = 0; v < 8 / VW; ++v) {
+            const V x = reinterpret_cast<const V*>(wq)[v];
+            if constexpr (VW == 4) { wz[4 * v] = x.x; wz[4 * v + 1] = x.y; wz[4 * v + 2] = x.z; wz[4 * v + 3] = x.w; }
+            else { wz[2 * v] = x.x; wz[2 * v + 1] = x.y; }
+          }
+#pragma unroll
+          for (int v = 0; v < CGP / VW; ++v) {
+            const V x = reinterpret_cast<const V*>(wq + kWSrc)[v];
+            if constexpr (VW == 4) {
+              str[4 * v] = x.x * wxy; str[4 * v + 1] = x.y * wxy; str[4 * v + 2] = x.z * wxy; str[4 * v + 3] = x.w * wxy;
+            } else {
+              str[2 * v] = x.x * wxy; str[2 * v + 1] = x.y * wxy;
+            }
+          }
 #pragma unroll
           for (int k = 0; k < kMaxW; ++k) {
             if (k < W) {
-              const T wz = wq[2 * kWS + k];
 #pragma unroll
-              for (int c = 0; c < CG; ++c) acc[k][c] += wz * str[c];
+              for (int c = 0; c < CG; ++c) acc[k][c] += wz[k] * str[c];
             }
           }
         }
@@ -182,20 +208,26 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
   }
   __syncthreads();
 
-  // add the tile to the periodic grid
+  // add the tile to the periodic grid: one warp per tile row
   const int b = a.bid[blockIdx.x];
   const int bx = b % a.nb, by = (b / a.nb) % a.nb, bz = b / (a.nb * a.nb);
   const int nf = a.nf;
   const long long P = (long long)nf * nf * nf;
-  const int lx = bx * kBin - W / 2 + nf, ly = by * kBin - W / 2 + nf, lz = bz * kBin - W / 2 + nf;
-  for (int c = 0; c < cg; ++c) {
-    T* Fc = a.F + (long long)(c0 + c) * P;
-    for (int i = tid; i < TV; i += kSpreadThreads) {
-      const T v = tile[c * TV + i];
+  const int lx = (bx * kBin - W / 2 + nf) % nf, ly = (by * kBin - W / 2 + nf) % nf,
+            lz = (bz * kBin - W / 2 + nf) % nf;
+  for (int row = warp; row < cg * TZ * TX; row += kSpreadThreads / 32) {
+    const int c = row / (TZ * TX), zy = row - c * TZ * TX, z = zy / TX, y = zy - z * TX;
+    int gy = ly + y, gz = lz + z;
+    gy -= gy >= nf ? nf : 0;
+    gz -= gz >= nf ? nf : 0;
+    T* Frow = a.F + (long long)(c0 + c) * P + ((long long)gz * nf + gy) * nf;
+    const T* trow = tile + c * TV + zy * TX;
+    for (int x = lane; x < TX; x += 32) {
+      const T v = trow[x];
       if (v == T(0)) continue;
-      const int x = i % TX, y = (i / TX) % TX, z = i / (TX * TX);
-      const int gx = (lx + x) % nf, gy = (ly + y) % nf, gz = (lz + z) % nf;
-      atomicAdd(&Fc[((long long)gz * nf + gy) * nf + gx], v);
+      int gx = lx + x;
+      gx -= gx >= nf ? nf : 0;
+      atomicAdd(&Frow[gx], v);
     }
   }
 }
@@ -426,10 +458,39 @@ struct mbo_surface_ctx {
   SurfStats* st = nullptr;
   SurfStats* h_st = nullptr;  // pinned
   size_t bytes = 0;
+  // per-pass timing (mbo_surface_profile_*)
+  bool prof = false;
+  struct Pending { int pass; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_free;
+  double prof_ms[MBO_SURFACE_PROFILE_PASSES] = {0};
+  long long prof_n[MBO_SURFACE_PROFILE_PASSES] = {0};
   char err[512] = {0};
 };
 
 namespace {
+
+cudaEvent_t take_event(mbo_surface_ctx* s) {
+  if (!s->ev_free.empty()) {
+    cudaEvent_t e = s->ev_free.back();
+    s->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Run f (a launch sequence on stream st); when profiling, bracket it with events.
+template <typename Fn> cudaError_t timed(mbo_surface_ctx* s, int pass, cudaStream_t st, Fn&& f) {
+  if (!s->prof) return f();
+  cudaEvent_t a = take_event(s), b = take_event(s);
+  cudaEventRecord(a, st);
+  const cudaError_t e = f();
+  cudaEventRecord(b, st);
+  s->pending.push_back({pass, a, b});
+  return e;
+}
 
 mbo_status sfail(mbo_surface_ctx* s, mbo_status rc, const char* fmt, const char* what = "") {
   if (s) snprintf(s->err, sizeof(s->err), fmt, what);
@@ -444,15 +505,21 @@ mbo_status sfail(mbo_surface_ctx* s, mbo_status rc, const char* fmt, const char*
                    "%s", cudaGetErrorString(e_));                                           \
   } while (0)
 
+// Shared bytes of a spreading block: the tile and the per-warp staging.
+size_t spread_smem(int cg, size_t elem, size_t tv) {
+  const size_t vw = 16 / elem;
+  const size_t chunk = elem == 4 ? chunk_of<float>() : chunk_of<double>();
+  const size_t stride = elem == 4 ? src_stride<float>() : src_stride<double>();
+  return (((size_t)cg * tv + vw - 1) / vw * vw + (size_t)(kSpreadThreads / 32) * chunk * stride) * elem;
+}
+
 // Channels per spreading block for n*n channels: the largest instantiated
-// group whose tile and staging fit in `limit` shared bytes (0 if none fits).
+// group that fits in `limit` shared bytes (0 if none fits).
 int spread_cg(int C, size_t elem, size_t tv, size_t limit) {
   const int cand[] = {9, 8, 4, 3, 1};
-  const size_t chunk = elem == 4 ? chunk_of<float>() : chunk_of<double>();
   for (int cg : cand) {
     if (cg > C || (elem == 8 && cg > 4)) continue;  // FP64: at most 4 (registers)
-    const size_t b = ((size_t)cg * tv + (size_t)(kSpreadThreads / 32) * chunk * (3 * kWS + cg)) * elem;
-    if (b <= limit) return cg;
+    if (spread_smem(cg, elem, tv) <= limit) return cg;
   }
   return 0;
 }
@@ -489,10 +556,13 @@ template <typename T> cudaError_t launch_spread(mbo_surface_ctx* s, const void* 
     case 1: return spread_run<T, 1>(a, grid, s->tile_bytes, st);
     case 3: return spread_run<T, 3>(a, grid, s->tile_bytes, st);
     case 4: return spread_run<T, 4>(a, grid, s->tile_bytes, st);
-    case 8: return spread_run<T, 8>(a, grid, s->tile_bytes, st);
-    case 9: return spread_run<T, 9>(a, grid, s->tile_bytes, st);
-    default: return cudaErrorInvalidValue;
+    default: break;
   }
+  if constexpr (sizeof(T) == 4) {  // FP64 groups stop at 4 channels (registers)
+    if (s->cg == 8) return spread_run<T, 8>(a, grid, s->tile_bytes, st);
+    if (s->cg == 9) return spread_run<T, 9>(a, grid, s->tile_bytes, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T, int NM> cudaError_t interp_run(const InterpArgs<T>& a, int groups, size_t smem,
@@ -552,11 +622,19 @@ mbo_status surface_diffusion(mbo_surface_ctx* s, const void* A, void* dst, bool 
   const long long P = (long long)s->prm.nf * s->prm.nf * s->prm.nf;
   const size_t elem = s->dtype == MBO_F32 ? 4 : 8;
   SCK(cudaMemsetAsync(s->F, 0, (size_t)s->C * P * elem, st));
-  SCK((s->dtype == MBO_F32 ? launch_spread<float>(s, A, st) : launch_spread<double>(s, A, st)));
-  const mbo_status rc = mbo_diffuse(s->fine, s->F, s->F, st);
+  SCK(timed(s, 0, st, [&] {
+    return s->dtype == MBO_F32 ? launch_spread<float>(s, A, st) : launch_spread<double>(s, A, st);
+  }));
+  mbo_status rc = MBO_OK;
+  timed(s, 1, st, [&] {
+    rc = mbo_diffuse(s->fine, s->F, s->F, st);
+    return cudaSuccess;
+  });
   if (rc != MBO_OK) return sfail(s, rc, "grid diffusion: %s", mbo_last_error(s->fine));
-  SCK((s->dtype == MBO_F32 ? launch_interp<float>(s, dst, scatter, st)
-                           : launch_interp<double>(s, dst, scatter, st)));
+  SCK(timed(s, 2, st, [&] {
+    return s->dtype == MBO_F32 ? launch_interp<float>(s, dst, scatter, st)
+                               : launch_interp<double>(s, dst, scatter, st);
+  }));
   return MBO_OK;
 }
 
@@ -659,6 +737,11 @@ mbo_status mbo_surface_destroy(mbo_surface s) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->h_st) cudaFreeHost(s->h_st);
+  for (auto& p : s->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : s->ev_free) cudaEventDestroy(e);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
   return MBO_OK;
@@ -794,8 +877,7 @@ mbo_status mbo_surface_create(mbo_surface* out, int64_t nq, const double* xq, co
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev);
   s->cg = spread_cg(s->C, elem, tv, (size_t)maxsm);
   s->chgroups = s->cg ? (s->C + s->cg - 1) / s->cg : 0;
-  const size_t chunk = elem == 4 ? chunk_of<float>() : chunk_of<double>();
-  s->tile_bytes = ((size_t)s->cg * tv + (size_t)(kSpreadThreads / 32) * chunk * (3 * kWS + s->cg)) * elem;
+  s->tile_bytes = spread_smem(s->cg, elem, tv);
   if (s->cg == 0) {
     mbo_surface_destroy(s);
     return MBO_ERR_UNSUPPORTED_SIZE;
@@ -896,7 +978,9 @@ mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stre
   mbo_status rc = surface_diffusion(s, A, s->At, false, st);
   if (rc != MBO_OK) return rc;
   SCK(cudaMemsetAsync(s->st, 0, sizeof(SurfStats), st));
-  SCK((s->dtype == MBO_F32 ? launch_project<float>(s, A, st) : launch_project<double>(s, A, st)));
+  SCK(timed(s, 3, st, [&] {
+    return s->dtype == MBO_F32 ? launch_project<float>(s, A, st) : launch_project<double>(s, A, st);
+  }));
   if (stats) {
     SCK(cudaMemcpyAsync(s->h_st, s->st, sizeof(SurfStats), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
@@ -911,6 +995,41 @@ mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stre
       snprintf(s->err, sizeof(s->err), "non-finite values in the projected field");
       return MBO_ERR_NUMERIC;
     }
+  }
+  return MBO_OK;
+}
+
+mbo_status mbo_surface_profile_enable(mbo_surface s, int enable) {
+  if (!s) return MBO_ERR_INVALID_ARG;
+  for (auto& p : s->pending) {
+    cudaEventSynchronize(p.b);
+    s->ev_free.push_back(p.a);
+    s->ev_free.push_back(p.b);
+  }
+  s->pending.clear();
+  for (int i = 0; i < MBO_SURFACE_PROFILE_PASSES; ++i) {
+    s->prof_ms[i] = 0;
+    s->prof_n[i] = 0;
+  }
+  s->prof = enable != 0;
+  return MBO_OK;
+}
+
+mbo_status mbo_surface_profile_read(mbo_surface s, double* ms, int64_t* launches, int npass) {
+  if (!s || npass < 0) return MBO_ERR_INVALID_ARG;
+  for (auto& p : s->pending) {
+    SCK(cudaEventSynchronize(p.b));
+    float t = 0.f;
+    SCK(cudaEventElapsedTime(&t, p.a, p.b));
+    s->prof_ms[p.pass] += t;
+    s->prof_n[p.pass] += 1;
+    s->ev_free.push_back(p.a);
+    s->ev_free.push_back(p.b);
+  }
+  s->pending.clear();
+  for (int i = 0; i < npass && i < MBO_SURFACE_PROFILE_PASSES; ++i) {
+    if (ms) ms[i] = s->prof_ms[i];
+    if (launches) launches[i] = s->prof_n[i];
   }
   return MBO_OK;
 }

@@ -25,6 +25,9 @@ experiments, Sec. 6.1, at the sizes the benchmark configurations name):
   * ``batch_mixed``   many independent 2-D fields of uneven sizes and orders.
   * ``paper_experiment`` the analytic initial fields of the paper's flat-torus
                       experiments (Sec. 6.1 examples 1-3, Sec. 7).
+  * ``sphere_paper_field`` the two printed 3x3 matrices of the sphere
+                      experiment (Sec. 6.2) placed on given surface points
+                      (raw: the matrices are not orthogonal as printed).
 """
 from __future__ import annotations
 
@@ -206,6 +209,24 @@ def paper_experiment(k: int, N: int = 1024):
 
 # Batched 2-D workload: field i gets N = SIZES[i % 7], n = 2 + (i % 2), tau = 4 / N^2.
 BATCH_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
+
+
+# The two matrices printed for the sphere experiment (Sec. 6.2), row-major.
+SPHERE_MATRICES = (
+    (0.392227, 0.706046, 0.046171, 0.655478, 0.031833, 0.097132, 0.171187, 0.276923, 0.82346),
+    (0.699077, 0.547216, 0.257508, 0.890903, 0.138624, 0.840717, 0.959291, 0.149294, 0.254282),
+)
+
+
+def sphere_paper_field(xc: np.ndarray) -> np.ndarray:
+    """Raw initial field of the sphere experiment (Sec. 6.2) at points xc
+    (nq x 3): the first printed matrix where x < 0, y < 0 and z > 0, the
+    second elsewhere.  Shape (9, nq)."""
+    xc = np.asarray(xc, dtype=np.float64)
+    sel = (xc[:, 0] < 0) & (xc[:, 1] < 0) & (xc[:, 2] > 0)
+    m1 = np.array(SPHERE_MATRICES[0]).reshape(9, 1)
+    m2 = np.array(SPHERE_MATRICES[1]).reshape(9, 1)
+    return np.where(sel[None, :], m1, m2)
 
 
 def batch_mixed(count: int, seed: int, sizes=BATCH_SIZES):

@@ -35,8 +35,11 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
 
 SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
                    "mbo_surface_create", "mbo_surface_destroy", "mbo_surface_get_params",
-                   "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_workspace_bytes",
+                   "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_profile_enable",
+                   "mbo_surface_profile_read", "mbo_surface_workspace_bytes",
                    "mbo_surface_last_error")
+
+SURFACE_PASSES = ("spread", "grid_fft", "interp", "project")
 
 MBO_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -139,13 +142,15 @@ def lib():
     L.mbo_surface_get_params.argtypes = [vp, C.POINTER(mbo_surface_params)]
     L.mbo_surface_diffuse.argtypes = [vp, vp, vp, vp]
     L.mbo_surface_step.argtypes = [vp, vp, C.POINTER(mbo_stats), vp]
+    L.mbo_surface_profile_enable.argtypes = [vp, C.c_int]
+    L.mbo_surface_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_surface_workspace_bytes.argtypes = [vp]
     L.mbo_surface_workspace_bytes.restype = C.c_int64
     L.mbo_surface_last_error.argtypes = [vp]
     L.mbo_surface_last_error.restype = C.c_char_p
     for f in ("mbo_surface_heat_modes", "mbo_surface_sphere_band", "mbo_surface_create",
               "mbo_surface_destroy", "mbo_surface_get_params", "mbo_surface_diffuse",
-              "mbo_surface_step"):
+              "mbo_surface_step", "mbo_surface_profile_enable", "mbo_surface_profile_read"):
         getattr(L, f).restype = C.c_int
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
               "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
@@ -495,6 +500,19 @@ def mbo_surface_step(s, A, want_stats: bool = False, stream=None):
     st = mbo_stats()
     _scheck(lib().mbo_surface_step(s, _ptr(A), C.byref(st) if want_stats else None, _stream(stream)), s)
     return st.as_dict() if want_stats else None
+
+
+def mbo_surface_profile_enable(s, enable: bool = True) -> None:
+    _scheck(lib().mbo_surface_profile_enable(s, 1 if enable else 0), s)
+
+
+def mbo_surface_profile_read(s) -> dict:
+    """{pass: (milliseconds, timed calls)} for the passes of SURFACE_PASSES."""
+    n = len(SURFACE_PASSES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _scheck(lib().mbo_surface_profile_read(s, ms, cnt, n), s)
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(SURFACE_PASSES)}
 
 
 def mbo_surface_workspace_bytes(s) -> int:
