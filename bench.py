@@ -534,8 +534,9 @@ def run_surface(args, ws, rank, local):
     from paper_1711_01365_gb300 import mbo as M
 
     tau, eps, dx, p, n = 0.005, 1e-6, 0.05, 3, 3
+    radius = args.surface_radius
     wb = M.mbo_surface_band_width(eps, tau)
-    xq, wq, xc = M.mbo_surface_sphere_band(1.0, dx, wb, p)
+    xq, wq, xc = M.mbo_surface_sphere_band(radius, dx, wb, p)
     nq = len(wq)
     s = M.Surface(xq, wq, xc, n, tau, eps, "f32")
     prm = s.params()
@@ -584,8 +585,8 @@ def run_surface(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": "unit sphere, closest-point band (Sec. 6.2): dx=0.05, tau=0.005, "
-                                       "eps=1e-6, p=3, n=3; the paper's two printed matrices as A_0",
+                "config": {"workload": f"sphere of radius {radius:g}, closest-point band (Sec. 6.2): dx=0.05, "
+                                       "tau=0.005, eps=1e-6, p=3, n=3; the paper's two printed matrices as A_0",
                            "points": nq, "band_width": wb, "h": prm["h"], "M": prm["M"],
                            "grid": prm["nf"], "kernel_width": W,
                            "l2": "grid and tables larger than L2 (no flush)",
@@ -611,6 +612,8 @@ def main():
     ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C5", "sphere"],
                     help="C2: 1024^2 headline (default); C3: 256^3, C5: 512^3 (FP32 only); "
                          "sphere: the closed-surface workload of Sec. 6.2")
+    ap.add_argument("--surface-radius", type=float, default=1.0,
+                    help="sphere radius of --workload sphere (1 = the paper's unit sphere)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
