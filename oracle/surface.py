@@ -19,6 +19,9 @@ What is computed, step by step, in the paper's order:
 * ``sphere_closest`` and ``sphere_band``: the closest-point map of a sphere and
   the sets G^b (grid points within w_b of the surface), Q (quadrature points)
   and the closest points x_q^c (Algorithm 2, step 1).
+* ``peanut_closest`` and ``peanut_band``: the same for the peanut surface of
+  Sec. 6.3, a surface of revolution whose closest points come from the
+  closest point of the generating curve in the point's meridian plane.
 * ``surface_diffuse``: steps 2-5 of Algorithm 2 as the plain double sum
       A*(x_t) = (h / 2 pi)^3 Re sum_m e^{-h^2 tau |m|^2} e^{i h m . x_t}
                                    sum_q w_q A~(x_q) e^{-i h m . x_q},
@@ -160,6 +163,83 @@ def sphere_band(radius: float, dx: float, wb: float, p: int):
     xq = (g[:, None, :] + off[None, :, :]).reshape(-1, 3)
     wq = np.tile(wq1, g.shape[0])
     return xq, wq, sphere_closest(xq, radius)
+
+
+# --- peanut geometry (Sec. 6.3; Algorithm 2, step 1) -------------------------------
+
+def peanut_curve(t):
+    """Generating curve of the peanut surface, t in [-1, 1]: x = 3t - t^3,
+    rho = sqrt((1 + x^2)(4 - x^2)) / 2 (the surface is (x, rho cos th, rho sin th))."""
+    t = np.asarray(t, dtype=np.float64)
+    x = 3 * t - t ** 3
+    rho = 0.5 * np.sqrt(np.maximum((1 + x * x) * (4 - x * x), 0.0))
+    return x, rho
+
+
+def peanut_closest(P: np.ndarray, samples: int = 20001, iters: int = 90, chunk: int = 4096):
+    """Closest point on the peanut surface of each row of P, through the
+    surface of revolution: the closest point of (x, r = |(y, z)|) on the
+    generating curve, by a dense scan of t and a golden-section search between
+    the neighbours of the best sample, rotated back to the point's meridian
+    ((y, z) = 0: the meridian of +y).  Returns (closest points, distances)."""
+    P = np.asarray(P, dtype=np.float64).reshape(-1, 3)
+    r = np.hypot(P[:, 1], P[:, 2])
+    ts = np.linspace(-1.0, 1.0, samples)
+    cx, cr = peanut_curve(ts)
+    tbest = np.empty(len(P))
+    for a in range(0, len(P), chunk):
+        b = min(len(P), a + chunk)
+        d2 = (cx[None, :] - P[a:b, 0:1]) ** 2 + (cr[None, :] - r[a:b, None]) ** 2
+        tbest[a:b] = ts[np.argmin(d2, axis=1)]
+    step = 2.0 / (samples - 1)
+    lo, hi = np.maximum(tbest - step, -1.0), np.minimum(tbest + step, 1.0)
+
+    def D(t):
+        x, rho = peanut_curve(t)
+        return (x - P[:, 0]) ** 2 + (rho - r) ** 2
+
+    g = (math.sqrt(5.0) - 1) / 2
+    c, d = hi - g * (hi - lo), lo + g * (hi - lo)
+    fc, fd = D(c), D(d)
+    for _ in range(iters):
+        left = fc < fd
+        hi = np.where(left, d, hi)
+        lo = np.where(left, lo, c)
+        c_new = hi - g * (hi - lo)
+        d_new = lo + g * (hi - lo)
+        c, d = np.where(left, c_new, d), np.where(left, c, d_new)
+        fc, fd = np.where(left, D(c), fd), np.where(left, fc, D(d))
+    t = 0.5 * (lo + hi)
+    x, rho = peanut_curve(t)
+    safe = np.where(r > 0, r, 1.0)
+    uy = np.where(r > 0, P[:, 1] / safe, 1.0)
+    uz = np.where(r > 0, P[:, 2] / safe, 0.0)
+    cp = np.stack([x, rho * uy, rho * uz], axis=1)
+    return cp, np.sqrt(D(t))
+
+
+def peanut_band(dx: float, wb: float, p: int):
+    """Band construction for the peanut (as ``sphere_band``): grid points
+    x_g = dx (i, j, k) whose distance to the surface is below wb, p^3
+    quadrature points per cell x_g + [0, dx]^3 with their weights, and the
+    closest points of the quadrature points.  Same ordering as sphere_band."""
+    t, w = cheb_rule(p)
+    s = dx * (1.0 + t) / 2.0
+    ws = w * dx / 2.0
+    _, cr = peanut_curve(np.linspace(-1, 1, 20001))
+    lx = int(math.ceil((2.0 + wb) / dx)) + 1
+    lr = int(math.ceil((cr.max() + wb) / dx)) + 1
+    I, J, K = np.meshgrid(np.arange(-lx, lx + 1), np.arange(-lr, lr + 1), np.arange(-lr, lr + 1), indexing="ij")
+    g = dx * np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1).astype(np.float64)
+    _, dist = peanut_closest(g)
+    g = g[dist < wb]
+    A, B, Cc = np.meshgrid(np.arange(p), np.arange(p), np.arange(p), indexing="ij")
+    a, b, c = A.ravel(), B.ravel(), Cc.ravel()
+    off = np.stack([s[a], s[b], s[c]], axis=1)
+    wq1 = ws[a] * ws[b] * ws[c]
+    xq = (g[:, None, :] + off[None, :, :]).reshape(-1, 3)
+    wq = np.tile(wq1, g.shape[0])
+    return xq, wq, peanut_closest(xq)[0]
 
 
 def extent(*pts) -> float:

@@ -186,3 +186,59 @@ def test_surface_step_keeps_a_constant_rotation():
     Bm = B[:, 0].reshape(3, 3)
     assert np.abs(Bm @ Bm.T - np.eye(3)).max() < 1e-12
     assert O.det(Bm) == pytest.approx(np.linalg.det(Q), abs=1e-12)
+
+
+def _peanut_surface_samples(nt=4001, nth=721):
+    t = np.linspace(-1, 1, nt)
+    x = 3 * t - t ** 3
+    rho = 0.5 * np.sqrt(np.maximum((1 + x * x) * (4 - x * x), 0))
+    th = np.linspace(0, 2 * np.pi, nth)
+    return np.stack([np.repeat(x, nth), np.outer(rho, np.cos(th)).ravel(), np.outer(rho, np.sin(th)).ravel()], 1)
+
+
+def _nearest_distance(samples, P):
+    """Distance from each row of P to the nearest sample (k-d tree query)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    return spatial.cKDTree(samples).query(P)[0]
+
+
+def test_peanut_closest_point_against_brute_force():
+    """Sec. 6.3: the closest point lies on the surface of revolution, and no
+    sample of a dense (t, theta) grid of the surface is closer."""
+    g = np.random.default_rng(7)
+    P = g.uniform(-3.2, 3.2, (150, 3))
+    cp, d = S.peanut_closest(P)
+    x, r = cp[:, 0], np.hypot(cp[:, 1], cp[:, 2])
+    assert np.abs(4 * r * r - (1 + x * x) * (4 - x * x)).max() < 1e-9
+    assert np.abs(np.linalg.norm(P - cp, axis=1) - d).max() < 1e-12
+    surf = _peanut_surface_samples()
+    brute = _nearest_distance(surf, P)
+    assert np.all(d <= brute + 1e-12)
+    # the meridian reduction: rotating the point about the x axis rotates its closest point
+    a = 0.7
+    Rx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+    cp2, d2 = S.peanut_closest(P @ Rx.T)
+    well = np.abs(P[:, 0]) > 1e-3  # x = 0: two mirror-image closest points may tie
+    assert np.abs(d2 - d).max() < 1e-12
+    assert np.abs(cp2[well] - cp[well] @ Rx.T).max() < 1e-7
+
+
+def test_peanut_band_cells_and_weights():
+    dx, wb, p = 0.4, 0.5, 2
+    xq, wq, xc = S.peanut_band(dx, wb, p)
+    ncell = len(wq) // p ** 3
+    assert wq.sum() == pytest.approx(ncell * dx ** 3, rel=1e-12)
+    corners = dx * np.round((xq[::p ** 3] - 0.5 * dx * (1 + np.cos(np.pi / (2 * p)))) / dx)  # first node: the largest
+    surf = _peanut_surface_samples(2001, 361)
+    dmin = _nearest_distance(surf, corners)
+    # every cell corner lies within wb of the surface (up to the sampling error
+    # of the brute-force distance), and the grid points just outside are absent
+    assert np.all(dmin < wb + 5e-3)
+    lx, lr = int(np.ceil((2 + wb) / dx)) + 1, int(np.ceil((1.2 + wb) / dx)) + 1
+    I, J, K = np.meshgrid(np.arange(-lx, lx + 1), np.arange(-lr, lr + 1), np.arange(-lr, lr + 1), indexing="ij")
+    grid = dx * np.stack([I.ravel(), J.ravel(), K.ravel()], 1)
+    dg = _nearest_distance(surf, grid)
+    inside = dg < wb - 5e-3
+    have = {tuple(np.round(c / dx).astype(int)) for c in corners}
+    assert all(tuple(np.round(q / dx).astype(int)) in have for q in grid[inside])
+    assert np.allclose(4 * np.hypot(xc[:, 1], xc[:, 2]) ** 2, (1 + xc[:, 0] ** 2) * (4 - xc[:, 0] ** 2), atol=1e-9)
