@@ -72,6 +72,16 @@ MBO_API mbo_status mbo_surface_sphere_band(double radius, double dx, double wb, 
                                            double* wq, double* xc, int64_t capacity,
                                            int64_t* count);
 
+/* The same for the peanut surface of Sec. 6.3: the surface of revolution about
+ * the x axis of the curve x = 3t - t^3, rho = sqrt((1 + x^2)(4 - x^2)) / 2,
+ * t in [-1, 1].  The band holds the grid points whose distance to the surface
+ * is below wb; closest points come from the closest point of (x, |(y, z)|) on
+ * the curve (a scan of t and a golden-section search; the +y meridian on the
+ * axis), so the band costs a few hundred curve evaluations per point.  Same
+ * arguments, order and errors as mbo_surface_sphere_band.  Host only. */
+MBO_API mbo_status mbo_surface_peanut_band(double dx, double wb, int p, double* xq, double* wq,
+                                           double* xc, int64_t capacity, int64_t* count);
+
 /* Plan one surface geometry.
  *   nq        number of quadrature points (= field points), 1 <= nq < 2^31.
  *   xq, wq    quadrature points (nq x 3) and weights (nq), host arrays.

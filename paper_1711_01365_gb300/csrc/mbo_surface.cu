@@ -418,6 +418,110 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// Band cells and quadrature points (Algorithm 2, step 1): the cells
+// x_g + [0, dx]^3 of the grid dx Z^3 with |i| <= li, |j|, |k| <= lr whose corner
+// x_g is in the band, each with p^3 points (the tensor product of the Chebyshev
+// nodes cos((2k - 1) pi / (2p)) mapped to [0, dx], with Fejer's first-rule
+// weights) and their closest points.  Order: cells (i, j, k) lexicographic, k
+// fastest, then the nodes (a, b, c), c fastest.  With any output NULL only the
+// count is produced.
+template <typename InBand, typename Closest>
+mbo_status emit_band(double dx, int p, long long li, long long lr, InBand in_band, Closest closest,
+                     double* xq, double* wq, double* xc, int64_t capacity, int64_t* count) {
+  std::vector<double> off(p), wc(p);
+  for (int k = 0; k < p; ++k) {
+    const double th = (2.0 * (k + 1) - 1.0) * M_PI / (2.0 * p);
+    double s = 0.0;
+    for (int j = 1; j <= p / 2; ++j) s += std::cos(2.0 * j * th) / (4.0 * j * j - 1.0);
+    off[k] = dx * (1.0 + std::cos(th)) / 2.0;
+    wc[k] = (2.0 / p) * (1.0 - 2.0 * s) * dx / 2.0;
+  }
+  const long long per = (long long)p * p * p;
+  int64_t n = 0;
+  const bool fill = xq && wq && xc;
+  for (long long i = -li; i <= li; ++i)
+    for (long long j = -lr; j <= lr; ++j)
+      for (long long k = -lr; k <= lr; ++k) {
+        const double gx = dx * i, gy = dx * j, gz = dx * k;
+        if (!in_band(gx, gy, gz)) continue;
+        if (fill && n + per <= capacity) {
+          for (int a = 0; a < p; ++a)
+            for (int b = 0; b < p; ++b)
+              for (int c = 0; c < p; ++c) {
+                const int64_t q = n + ((int64_t)a * p + b) * p + c;
+                xq[3 * q] = gx + off[a];
+                xq[3 * q + 1] = gy + off[b];
+                xq[3 * q + 2] = gz + off[c];
+                wq[q] = wc[a] * wc[b] * wc[c];
+                closest(xq[3 * q], xq[3 * q + 1], xq[3 * q + 2], xc + 3 * q);
+              }
+        }
+        n += per;
+      }
+  *count = n;
+  if (fill && n > capacity) return MBO_ERR_INVALID_ARG;
+  return MBO_OK;
+}
+
+// Generating curve of the peanut surface (Sec. 6.3), t in [-1, 1]: x = 3t - t^3
+// and rho = sqrt((1 + x^2)(4 - x^2)) / 2, written as (1 - t^2) sqrt((1 + x^2)(4 - t^2)) / 2
+// (4 - x^2 = (1 - t^2)^2 (4 - t^2)), which stays real to the ends.
+void peanut_curve(double t, double& x, double& rho) {
+  x = 3.0 * t - t * t * t;
+  rho = 0.5 * (1.0 - t * t) * std::sqrt((1.0 + x * x) * (4.0 - t * t));
+}
+
+// Closest point c on the peanut surface to (x, y, z) and its distance.  The
+// surface is one of revolution about the x axis, so the closest point is that of
+// (x, |(y, z)|) on the generating curve, turned into the point's meridian (the
+// +y meridian on the axis): a scan of 257 values of t, then a golden-section
+// search between the neighbours of the nearest one.
+double peanut_closest(double px, double py, double pz, double* c) {
+  const double r = std::sqrt(py * py + pz * pz);
+  auto D = [&](double t) {
+    double x, rho;
+    peanut_curve(t, x, rho);
+    return (x - px) * (x - px) + (rho - r) * (rho - r);
+  };
+  constexpr int kScan = 257;
+  int best = 0;
+  double dbest = D(-1.0);
+  for (int i = 1; i < kScan; ++i) {
+    const double d = D(-1.0 + 2.0 * i / (kScan - 1));
+    if (d < dbest) {
+      dbest = d;
+      best = i;
+    }
+  }
+  const double step = 2.0 / (kScan - 1);
+  double lo = std::max(-1.0, -1.0 + step * (best - 1)), hi = std::min(1.0, -1.0 + step * (best + 1));
+  const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+  double a = hi - g * (hi - lo), b = lo + g * (hi - lo), fa = D(a), fb = D(b);
+  for (int it = 0; it < 80; ++it) {
+    if (fa < fb) {
+      hi = b;
+      b = a;
+      fb = fa;
+      a = hi - g * (hi - lo);
+      fa = D(a);
+    } else {
+      lo = a;
+      a = b;
+      fa = fb;
+      b = lo + g * (hi - lo);
+      fb = D(b);
+    }
+  }
+  const double t = 0.5 * (lo + hi);
+  double x, rho;
+  peanut_curve(t, x, rho);
+  const double uy = r > 0 ? py / r : 1.0, uz = r > 0 ? pz / r : 0.0;
+  c[0] = x;
+  c[1] = rho * uy;
+  c[2] = rho * uz;
+  return std::sqrt(D(t));
+}
+
 bool smooth23(int N) {
   while (N % 2 == 0) N /= 2;
   while (N % 3 == 0) N /= 3;
@@ -673,56 +777,42 @@ mbo_status mbo_surface_heat_modes(double eps, double tau, double R, double* h, i
 mbo_status mbo_surface_sphere_band(double radius, double dx, double wb, int p, double* xq,
                                    double* wq, double* xc, int64_t capacity, int64_t* count) {
   if (!(radius > 0) || !(dx > 0) || !(wb > 0) || p < 1 || p > 16 || !count) return MBO_ERR_INVALID_ARG;
-  // nodes cos((2k - 1) pi / (2p)) and Fejer's first-rule weights on [-1, 1]
-  std::vector<double> t(p), w(p);
-  for (int k = 0; k < p; ++k) {
-    const double th = (2.0 * (k + 1) - 1.0) * M_PI / (2.0 * p);
-    t[k] = std::cos(th);
-    double s = 0.0;
-    for (int j = 1; j <= p / 2; ++j) s += std::cos(2.0 * j * th) / (4.0 * j * j - 1.0);
-    w[k] = (2.0 / p) * (1.0 - 2.0 * s);
-  }
-  std::vector<double> off(p), wc(p);
-  for (int k = 0; k < p; ++k) {
-    off[k] = dx * (1.0 + t[k]) / 2.0;
-    wc[k] = w[k] * dx / 2.0;
-  }
   const long long lim = (long long)std::ceil((radius + wb) / dx) + 1;
-  const long long per = (long long)p * p * p;
-  int64_t n = 0;
-  const bool fill = xq && wq && xc;
-  for (long long i = -lim; i <= lim; ++i)
-    for (long long j = -lim; j <= lim; ++j)
-      for (long long k = -lim; k <= lim; ++k) {
-        const double gx = dx * i, gy = dx * j, gz = dx * k;
-        if (!(std::fabs(std::sqrt(gx * gx + gy * gy + gz * gz) - radius) < wb)) continue;
-        if (fill && n + per <= capacity) {
-          for (int a = 0; a < p; ++a)
-            for (int b = 0; b < p; ++b)
-              for (int c = 0; c < p; ++c) {
-                const int64_t q = n + ((int64_t)a * p + b) * p + c;
-                const double x = gx + off[a], y = gy + off[b], z = gz + off[c];
-                xq[3 * q] = x;
-                xq[3 * q + 1] = y;
-                xq[3 * q + 2] = z;
-                wq[q] = wc[a] * wc[b] * wc[c];
-                const double r = std::sqrt(x * x + y * y + z * z);
-                if (r > 0) {
-                  xc[3 * q] = radius * x / r;
-                  xc[3 * q + 1] = radius * y / r;
-                  xc[3 * q + 2] = radius * z / r;
-                } else {
-                  xc[3 * q] = 0.0;
-                  xc[3 * q + 1] = 0.0;
-                  xc[3 * q + 2] = radius;
-                }
-              }
-        }
-        n += per;
-      }
-  *count = n;
-  if (fill && n > capacity) return MBO_ERR_INVALID_ARG;
-  return MBO_OK;
+  auto in_band = [&](double x, double y, double z) {
+    return std::fabs(std::sqrt(x * x + y * y + z * z) - radius) < wb;
+  };
+  auto closest = [&](double x, double y, double z, double* c) {
+    const double r = std::sqrt(x * x + y * y + z * z);
+    if (r > 0) {
+      c[0] = radius * x / r;
+      c[1] = radius * y / r;
+      c[2] = radius * z / r;
+    } else {
+      c[0] = 0.0;
+      c[1] = 0.0;
+      c[2] = radius;
+    }
+  };
+  return emit_band(dx, p, lim, lim, in_band, closest, xq, wq, xc, capacity, count);
+}
+
+mbo_status mbo_surface_peanut_band(double dx, double wb, int p, double* xq, double* wq, double* xc,
+                                   int64_t capacity, int64_t* count) {
+  if (!(dx > 0) || !(wb > 0) || p < 1 || p > 16 || !count) return MBO_ERR_INVALID_ARG;
+  double rho_max = 0.0;
+  for (int i = 0; i <= 4096; ++i) {
+    double x, rho;
+    peanut_curve(-1.0 + 2.0 * i / 4096, x, rho);
+    rho_max = std::max(rho_max, rho);
+  }
+  const long long lx = (long long)std::ceil((2.0 + wb) / dx) + 1;
+  const long long lr = (long long)std::ceil((rho_max + wb) / dx) + 1;
+  auto in_band = [&](double x, double y, double z) {
+    double c[3];
+    return peanut_closest(x, y, z, c) < wb;
+  };
+  auto closest = [&](double x, double y, double z, double* c) { peanut_closest(x, y, z, c); };
+  return emit_band(dx, p, lx, lr, in_band, closest, xq, wq, xc, capacity, count);
 }
 
 mbo_status mbo_surface_destroy(mbo_surface s) {

@@ -34,6 +34,7 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
            "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
 
 SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
+                   "mbo_surface_peanut_band",
                    "mbo_surface_create", "mbo_surface_destroy", "mbo_surface_get_params",
                    "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_profile_enable",
                    "mbo_surface_profile_read", "mbo_surface_workspace_bytes",
@@ -136,6 +137,7 @@ def lib():
     L.mbo_surface_heat_modes.argtypes = [C.c_double, C.c_double, C.c_double, dp, C.POINTER(C.c_int)]
     L.mbo_surface_sphere_band.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, vp, vp, vp,
                                           C.c_int64, i64p]
+    L.mbo_surface_peanut_band.argtypes = [C.c_double, C.c_double, C.c_int, vp, vp, vp, C.c_int64, i64p]
     L.mbo_surface_create.argtypes = [C.POINTER(vp), C.c_int64, vp, vp, vp, C.c_int, C.c_double,
                                      C.c_double, C.c_int]
     L.mbo_surface_destroy.argtypes = [vp]
@@ -148,7 +150,7 @@ def lib():
     L.mbo_surface_workspace_bytes.restype = C.c_int64
     L.mbo_surface_last_error.argtypes = [vp]
     L.mbo_surface_last_error.restype = C.c_char_p
-    for f in ("mbo_surface_heat_modes", "mbo_surface_sphere_band", "mbo_surface_create",
+    for f in ("mbo_surface_heat_modes", "mbo_surface_sphere_band", "mbo_surface_peanut_band", "mbo_surface_create",
               "mbo_surface_destroy", "mbo_surface_get_params", "mbo_surface_diffuse",
               "mbo_surface_step", "mbo_surface_profile_enable", "mbo_surface_profile_read"):
         getattr(L, f).restype = C.c_int
@@ -469,6 +471,17 @@ def mbo_surface_sphere_band(radius: float, dx: float, wb: float, p: int):
     xq, wq, xc = np.empty((n, 3)), np.empty(n), np.empty((n, 3))
     _scheck(lib().mbo_surface_sphere_band(float(radius), float(dx), float(wb), int(p), xq.ctypes.data,
                                           wq.ctypes.data, xc.ctypes.data, n, C.byref(cnt)))
+    return xq, wq, xc
+
+
+def mbo_surface_peanut_band(dx: float, wb: float, p: int):
+    """(xq, wq, xc) host arrays of the peanut band (count query, then fill)."""
+    cnt = C.c_int64()
+    _scheck(lib().mbo_surface_peanut_band(float(dx), float(wb), int(p), None, None, None, 0, C.byref(cnt)))
+    n = cnt.value
+    xq, wq, xc = np.empty((n, 3)), np.empty(n), np.empty((n, 3))
+    _scheck(lib().mbo_surface_peanut_band(float(dx), float(wb), int(p), xq.ctypes.data, wq.ctypes.data,
+                                          xc.ctypes.data, n, C.byref(cnt)))
     return xq, wq, xc
 
 

@@ -192,3 +192,26 @@ def test_full_size_sphere_properties(M):
     assert np.abs(B[:, far] - q2.reshape(9, 1)).max() < 1e-4
     assert st["det_flips"] == int(np.sum(np.sign(d) != np.sign(np.linalg.det(_mats(A, 3)))))
     s.close()
+
+
+def test_coarse_peanut_band(M):
+    """The peanut of Sec. 6.3 (tau = 0.032, eps = 1e-6 as printed; coarse
+    cells dx = 0.35, p = 1): diffusion against the oracle's double sum on the
+    library's band, and one step that stays orthogonal."""
+    tau, eps, n = 0.032, 1e-6, 2
+    wb = M.mbo_surface_band_width(eps, tau)
+    xq, wq, xc = M.mbo_surface_peanut_band(0.35, wb, 1)
+    A = field(n, len(wq), 44)
+    s = M.Surface(xq, wq, xc, n, tau, eps, "f32")
+    p = s.params()
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(a)
+    s.diffuse(a, out)
+    torch.cuda.synchronize()
+    ref = S.surface_diffuse(A, xq, wq, xc, tau, p["h"], p["M"])
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= TOL["f32"] * max(1.0, np.abs(ref).max())
+    st = s.step(a, want_stats=True)
+    Bm = _mats(a.double().cpu().numpy(), n)
+    assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < 2e-6
+    assert st["nonfinite"] == 0
+    s.close()

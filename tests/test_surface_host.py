@@ -1,7 +1,7 @@
 """Host logic of the closed-surface entry points (include/mbo_surface.h), on
-the CPU: the band width, the heat-kernel modes and the sphere band that the
-library computes on the host (Algorithm 2, step 1) agree with the oracle, and
-bad arguments are rejected before any device call."""
+the CPU: the band width, the heat-kernel modes and the sphere and peanut bands
+that the library computes on the host (Algorithm 2, step 1) agree with the
+oracle, and bad arguments are rejected before any device call."""
 import math
 
 import numpy as np
@@ -47,6 +47,8 @@ def test_bad_arguments_rejected(lib):
     assert ei.value.status == 1
     with pytest.raises(M.MboError):
         M.mbo_surface_sphere_band(1.0, 0.0, 0.5, 2)
+    with pytest.raises(M.MboError):
+        M.mbo_surface_peanut_band(0.3, -1.0, 2)
     pts = np.zeros((4, 3))
     w = np.ones(4)
     for args in [(pts, w, pts, 0, 0.01, 1e-6), (pts, w, pts, 5, 0.01, 1e-6), (pts, w, pts, 2, 0.0, 1e-6),
@@ -59,3 +61,17 @@ def test_bad_arguments_rejected(lib):
     with pytest.raises(M.MboError) as ei:
         M.mbo_surface_create(bad, w, pts, 2, 0.01, 1e-6)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("dx,wb,p", [(0.4, 0.53, 2), (0.35, 1.07, 1), (0.3, 0.77, 2)])
+def test_peanut_band_matches_the_oracle(lib, dx, wb, p):
+    """Sec. 6.3: the library's peanut band (closest points by its own curve scan
+    and golden-section search) against the oracle's.  The search stops at
+    ~1e-8 in t, so closest points agree to 1e-6; band widths are chosen away
+    from exact ties (a grid point whose distance equals wb)."""
+    xq, wq, xc = M.mbo_surface_peanut_band(dx, wb, p)
+    oq, ow, oc = S.peanut_band(dx, wb, p)
+    assert xq.shape == oq.shape
+    assert np.abs(xq - oq).max() < 1e-13
+    assert np.abs(wq - ow).max() < 1e-15
+    assert np.abs(xc - oc).max() < 1e-6
