@@ -100,11 +100,13 @@ template <typename T> struct SpreadArgs {
 // warp hit distinct banks); then lane p of round rd owns footprint column
 // (x, y) = (p % (W+1), p / (W+1)), p = lane + 32 rd, sums it over the chunk, W
 // points along z for CG channels in registers, and adds it to the bin tile.
+// WT: the kernel width as a compile-time constant (the width of eps = 1e-6,
+// the paper's choice, has its own instantiation), or 0 for the runtime width.
 template <typename T> __host__ __device__ constexpr int chunk_of() { return sizeof(T) == 4 ? 32 : 16; }
 constexpr int kWS = 9;     // weight slots of x and of y per source (>= W + 1)
 constexpr int kWSrc = 28;  // per source: z[8] | x[kWS] | y[kWS] | 2 pad, then strengths
 template <typename T> __host__ __device__ constexpr int src_stride() { return sizeof(T) == 4 ? 44 : 34; }
-template <typename T, int CG>
+template <typename T, int CG, int WT>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int CH = chunk_of<T>(), SRC = src_stride<T>();
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
   constexpr int CGP = (CG + VW - 1) / VW * VW;
   static_assert(kWSrc + CGP <= SRC, "strengths must fit the source stride");
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int W = a.W, FW = W + 1, TX = kBin + FW, TZ = kBin + W, TV = TX * TX * TZ;
+  const int W = WT ? WT : a.W, FW = W + 1, TX = kBin + FW, TZ = kBin + W, TV = TX * TX * TZ;
   T* tile = reinterpret_cast<T*>(smem_raw);  // [c][z][y][x], TX x TX x TZ
   const int c0 = blockIdx.y * CG;
   const int cg = min(CG, a.C - c0);
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
           for (int k = 0; k < kMaxW; ++k) {
             if (k < W) {
 #pragma unroll
-              for (int c = 0; c < CG; ++c)
-                if (c < cg) atomicAdd(&tile[c * TV + addr], acc[k][c]);
+              for (int c = 0; c < CG; ++c)  // channels past cg add their zeros
+                atomicAdd(&tile[c * TV + addr], acc[k][c]);
             }
             addr += TX * TX;
           }
@@ -253,12 +255,12 @@ constexpr int kInterpBlock = 128;
 template <typename T, int C> __host__ __device__ constexpr int padded_channels() {
   return C == 1 ? 1 : (sizeof(T) == 4 ? (C + 3) / 4 * 4 : (C + 1) / 2 * 2);
 }
-template <typename T, int NM>
+template <typename T, int NM, int WT>
 __global__ void __launch_bounds__(kInterpBlock) k_interp(InterpArgs<T> a) {
   constexpr int C = NM * NM, CP = padded_channels<T, C>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* fp = reinterpret_cast<T*>(smem_raw);  // [W^3][CP]
-  const int W = a.W, W2 = W * W, W3 = W2 * W, nf = a.nf;
+  const int W = WT ? WT : a.W, W2 = W * W, W3 = W2 * W, nf = a.nf;
   const long long P = (long long)nf * nf * nf;
   const int g = blockIdx.x;
   const int4 g0 = a.tg0[g];
@@ -630,7 +632,7 @@ int spread_cg(int C, size_t elem, size_t tv, size_t limit) {
 
 template <typename T, int CG> cudaError_t spread_run(const SpreadArgs<T>& a, dim3 grid, size_t smem,
                                                      cudaStream_t st) {
-  auto k = k_spread<T, CG>;
+  auto k = a.W == 7 ? k_spread<T, CG, 7> : k_spread<T, CG, 0>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -671,7 +673,7 @@ template <typename T> cudaError_t launch_spread(mbo_surface_ctx* s, const void* 
 
 template <typename T, int NM> cudaError_t interp_run(const InterpArgs<T>& a, int groups, size_t smem,
                                                       cudaStream_t st) {
-  auto k = k_interp<T, NM>;
+  auto k = a.W == 7 ? k_interp<T, NM, 7> : k_interp<T, NM, 0>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -215,3 +215,22 @@ def test_coarse_peanut_band(M):
     assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < 2e-6
     assert st["nonfinite"] == 0
     s.close()
+
+
+def test_runtime_width_fp32(M):
+    """eps = 1e-4 gives width 5, which runs the runtime-width kernels (width 7,
+    the paper's eps = 1e-6, has its own compile-time instantiation): diffusion
+    against the double sum to the accuracy of that width (~10^(1 - 5))."""
+    nq, tau, eps, n = 1501, 0.01, 1e-4, 3
+    xq, wq, xc = clustered(nq, 55)
+    A = field(n, nq, 56)
+    s = M.Surface(xq, wq, xc, n, tau, eps, "f32")
+    p = s.params()
+    assert p["width"] == 5
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(a)
+    s.diffuse(a, out)
+    torch.cuda.synchronize()
+    ref = S.surface_diffuse(A, xq, wq, xc, tau, p["h"], p["M"])
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= 1e-3 * max(1.0, np.abs(ref).max())
+    s.close()
