@@ -103,6 +103,13 @@ template <typename T> struct SpreadArgs {
 // WT: the kernel width as a compile-time constant (the width of eps = 1e-6,
 // the paper's choice, has its own instantiation), or 0 for the runtime width.
 template <typename T> __host__ __device__ constexpr int chunk_of() { return sizeof(T) == 4 ? 32 : 16; }
+// Tile column of x in tile row y.  At width 7 the rows are 16 wide and a flush
+// writes 4 rows x 8 columns from an even (x, y) start: x ^ 8 on rows with bit 1
+// of y set puts those 32 lanes on 32 distinct banks.
+template <int WT> __device__ __forceinline__ int swz(int x, int y) {
+  if constexpr (WT == 7) return x ^ (((y >> 1) & 1) << 3);
+  return x;
+}
 constexpr int kWS = 9;     // weight slots of x and of y per source (>= W + 1)
 constexpr int kWSrc = 28;  // per source: z[8] | x[kWS] | y[kWS] | 2 pad, then strengths
 template <typename T> __host__ __device__ constexpr int src_stride() { return sizeof(T) == 4 ? 44 : 34; }
@@ -179,22 +186,20 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < CGP / VW; ++v) {
             const V x = reinterpret_cast<const V*>(wq + kWSrc)[v];
-            if constexpr (VW == 4) {
-              str[4 * v] = x.x * wxy; str[4 * v + 1] = x.y * wxy; str[4 * v + 2] = x.z * wxy; str[4 * v + 3] = x.w * wxy;
-            } else {
-              str[2 * v] = x.x * wxy; str[2 * v + 1] = x.y * wxy;
-            }
+            if constexpr (VW == 4) { str[4 * v] = x.x; str[4 * v + 1] = x.y; str[4 * v + 2] = x.z; str[4 * v + 3] = x.w; }
+            else { str[2 * v] = x.x; str[2 * v + 1] = x.y; }
           }
 #pragma unroll
           for (int k = 0; k < kMaxW; ++k) {
             if (k < W) {
+              const T w = wz[k] * wxy;
 #pragma unroll
-              for (int c = 0; c < CG; ++c) acc[k][c] += wz[k] * str[c];
+              for (int c = 0; c < CG; ++c) acc[k][c] += w * str[c];
             }
           }
         }
         if (ok) {
-          int addr = (tz * TX + ty + j) * TX + tx + i;
+          int addr = (tz * TX + ty + j) * TX + swz<WT>(tx + i, ty + j);
 #pragma unroll
           for (int k = 0; k < kMaxW; ++k) {
             if (k < W) {
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a) {
     T* Frow = a.F + (long long)(c0 + c) * P + ((long long)gz * nf + gy) * nf;
     const T* trow = tile + c * TV + zy * TX;
     for (int x = lane; x < TX; x += 32) {
-      const T v = trow[x];
+      const T v = trow[swz<WT>(x, y)];
       if (v == T(0)) continue;
       int gx = lx + x;
       gx -= gx >= nf ? nf : 0;
