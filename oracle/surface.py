@@ -318,3 +318,31 @@ def surface_step(A: np.ndarray, xs: np.ndarray, ws: np.ndarray, xt: np.ndarray, 
     d0 = np.array([np.linalg.det(A0[:, i].reshape(n, n)) for i in range(A0.shape[1])])
     flips = int(np.sum((d0 > 0) != (sg > 0)))
     return B, At, {"max_delta": float(np.abs(B - A0).max()), "det_flips": flips}
+
+
+# --- volume-preserving step on the surface (Sec. 7 on a closed surface) ---------
+
+def surface_step_volume(A: np.ndarray, xs: np.ndarray, ws: np.ndarray, xt: np.ndarray, n: int,
+                        tau: float, h: float, M: int, n_plus: int = -1):
+    """One volume-preserving step (Sec. 7) with the surface diffusion of
+    Algorithm 2: A~ = surface_diffuse(A); dE(x) = <T+(A~) - T-(A~), A~> per
+    point (T+/T- the closest matrices of SO(n) / SO^-(n), Lemma 7.1); the n_plus
+    points of largest dE (equal dE: lower point index first) take T+, the rest
+    T- (Lemma 7.2 with one unit of volume per point, the threshold form of
+    Algorithm 3).  n_plus < 0: the number of points with det A > 0.  Returns
+    (A_next, A~, dE, stats)."""
+    A0 = np.asarray(A, dtype=np.float64)
+    At = surface_diffuse(A0, xs, ws, xt, tau, h, M)
+    npt = At.shape[1]
+    mats = At.T.reshape(npt, n, n)
+    dE = np.array([_core.delta_energy(m) for m in mats])
+    if n_plus < 0:
+        n_plus = _core.count_positive(A0, n)
+    order = np.lexsort((np.arange(npt), -dE))
+    plus = np.zeros(npt, dtype=bool)
+    plus[order[:n_plus]] = True
+    B = np.stack([_core.polar_class(m, 1 if p else -1).reshape(-1) for m, p in zip(mats, plus)], axis=1)
+    d0 = np.array([np.linalg.det(A0[:, i].reshape(n, n)) for i in range(npt)])
+    stats = {"max_delta": float(np.abs(B - A0).max()), "det_flips": int(np.sum((d0 > 0) != plus)),
+             "n_plus": int(n_plus)}
+    return B, At, dE, stats

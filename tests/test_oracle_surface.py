@@ -242,3 +242,43 @@ def test_peanut_band_cells_and_weights():
     have = {tuple(np.round(c / dx).astype(int)) for c in corners}
     assert all(tuple(np.round(q / dx).astype(int)) in have for q in grid[inside])
     assert np.allclose(4 * np.hypot(xc[:, 1], xc[:, 2]) ** 2, (1 + xc[:, 0] ** 2) * (4 - xc[:, 0] ** 2), atol=1e-9)
+
+
+def _small_surface_case(npts, seed, n):
+    g = np.random.default_rng(seed)
+    xs = g.uniform(0, 1, (npts, 3))
+    xt = np.clip(xs + g.normal(0, 0.05, xs.shape), 0, 1)
+    ws = g.uniform(0.5, 1.5, npts) / npts
+    A = O.project(g.standard_normal((n * n, 1)) + 0.9 * g.standard_normal((n * n, npts)), n)
+    h, M = S.heat_modes(1e-6, 0.02, S.extent(xs, xt))
+    return A, xs, ws, xt, h, M
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_surface_volume_step_is_the_constrained_optimum(n):
+    """Sec. 7, Lemma 7.2: with one unit of volume per point the selection
+    maximises sum <T_class(x), A~(x)> over all assignments with n_plus points in
+    SO(n) (brute force over every subset of a tiny point set), keeps that count,
+    and equals the plain step when n_plus is the plain step's own count."""
+    import itertools
+    A, xs, ws, xt, h, M = _small_surface_case(10, 40 + n, n)
+    B, At, dE, st = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, n_plus=4)
+    mats = At.T.reshape(-1, n, n)
+    tp = np.stack([O.polar_class(m, 1).reshape(-1) for m in mats], 1)
+    tm = np.stack([O.polar_class(m, -1).reshape(-1) for m in mats], 1)
+    gain = (tp * At).sum(0) - (tm * At).sum(0)
+    assert np.allclose(gain, dE, atol=1e-12)
+    best = max(sum(gain[list(c)]) for c in itertools.combinations(range(10), 4))
+    sel = np.array([np.linalg.det(B[:, i].reshape(n, n)) > 0 for i in range(10)])
+    assert sel.sum() == 4
+    assert gain[sel].sum() == pytest.approx(best, abs=1e-12)
+    Bm = B.T.reshape(-1, n, n)
+    assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < 1e-12
+    # the plain step's own count reproduces the plain step
+    Bp, _, _ = S.surface_step(A, xs, ws, xt, n, 0.02, h, M)
+    k = int(sum(np.linalg.det(Bp[:, i].reshape(n, n)) > 0 for i in range(10)))
+    Bv, _, _, _ = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, n_plus=k)
+    assert np.abs(Bv - Bp).max() < 1e-12
+    # n_plus < 0 keeps the input's count
+    _, _, _, st2 = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M)
+    assert st2["n_plus"] == O.count_positive(A, n)
