@@ -125,6 +125,18 @@ MBO_API mbo_status mbo_surface_diffuse(mbo_surface s, const void* A, void* A_til
  * energy is NaN (the surface path defines no Lyapunov value). */
 MBO_API mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stream);
 
+/* One volume-preserving step on the surface (Sec. 7 with the diffusion above),
+ * in place: the n_plus points of largest dE = <T+ - T-, A~> (T+, T- the
+ * closest matrices of SO(n) and SO^-(n) to the diffused A~, Lemma 7.1) take
+ * T+, the others T- (Lemma 7.2 with one unit of volume per point; equal dE:
+ * lower point index first).  n_plus < 0: the number of points with
+ * det A > 0 in the input, so that repeated steps keep the count.  n <= 3
+ * (MBO_ERR_UNSUPPORTED_SIZE otherwise); n_plus > nq is MBO_ERR_INVALID_ARG.
+ * stats as in mbo_surface_step (fallback_points 0).  Allocates 2 n*n nq
+ * elements and nq keys on first use. */
+MBO_API mbo_status mbo_surface_step_volume(mbo_surface s, void* A, int64_t n_plus, mbo_stats* stats,
+                                           void* stream);
+
 /* Per-pass device timing of the surface calls (CUDA events around each
  * launch on the caller's stream; off by default).  Passes, in this order:
  * spreading (k_spread), the grid's FFT diffusion (all its passes together),

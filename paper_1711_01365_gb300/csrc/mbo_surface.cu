@@ -393,6 +393,40 @@ __global__ void __launch_bounds__(kProjThreads) k_sproject(ProjArgs<T> a) {
   }
 }
 
+// Step statistics of the volume-preserving step: compare the previous field
+// with the assigned one, point by point (both in the caller's order).
+template <typename T, int NM>
+__global__ void __launch_bounds__(kProjThreads) k_sdelta(const T* old, const T* A, long long nq, SurfStats* st) {
+  constexpr int C = NM * NM;
+  __shared__ double redd[32];
+  __shared__ int redi[32];
+  const long long q = (long long)blockIdx.x * kProjThreads + threadIdx.x;
+  PointStats<T> ps;
+  if (q < nq) {
+    T o[C], b[C];
+    bool fin = true;
+    T d = T(0);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      o[c] = old[c * nq + q];
+      b[c] = A[c * nq + q];
+      fin = fin && isfinite(b[c]);
+      d = fmax(d, fabs(b[c] - o[c]));
+    }
+    ps.maxd = d;
+    ps.nonfinite = fin ? 0 : 1;
+    ps.flips = (det_sign<NM>(o) != det_sign<NM>(b)) ? 1 : 0;
+  }
+  const double mx = block_max((double)ps.maxd, redd);
+  const int fl = block_sum(ps.flips, redi);
+  const int nfin = block_sum(ps.nonfinite, redi);
+  if (threadIdx.x == 0) {
+    atomicMax(&st->maxd_bits, (unsigned long long)__double_as_longlong(mx));
+    if (fl) atomicAdd(&st->flips, (unsigned long long)fl);
+    if (nfin) atomicAdd(&st->nonfinite, (unsigned long long)nfin);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // host-side geometry (Algorithm 2, step 1) and plan parameters
 // ----------------------------------------------------------------------------
@@ -556,6 +590,10 @@ struct mbo_surface_ctx {
   mbo_handle fine = nullptr;  // 3-D FFT diffusion on the nf^3 grid
   void* F = nullptr;          // grid, C x nf^3
   void* At = nullptr;         // diffused values in sorted target order, C x nq
+  // volume-preserving step (allocated on first use)
+  void* Au = nullptr;                      // diffused values in the caller's order, C x nq
+  unsigned long long* vkeys = nullptr;     // one selection key per point
+  SelectState* vss = nullptr;
   void* su = nullptr;         // V4<T> sources
   int* sidx = nullptr;
   int* gsrc = nullptr;
@@ -830,7 +868,7 @@ mbo_status mbo_surface_destroy(mbo_surface s) {
   cudaDeviceSynchronize();
   if (s->fine) mbo_destroy(s->fine);
   void* bufs[] = {s->F, s->At, s->su, s->sidx, s->gsrc, s->gt0, s->bgrp, s->bid,
-                  s->tu, s->tidx, s->tgrp, s->tg0, s->st};
+                  s->tu, s->tidx, s->tgrp, s->tg0, s->st, s->Au, s->vkeys, s->vss};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->h_st) cudaFreeHost(s->h_st);
@@ -1090,6 +1128,75 @@ mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stre
     stats->nonfinite = (int64_t)s->h_st->nonfinite;
     if (stats->nonfinite) {
       snprintf(s->err, sizeof(s->err), "non-finite values in the projected field");
+      return MBO_ERR_NUMERIC;
+    }
+  }
+  return MBO_OK;
+}
+
+mbo_status mbo_surface_step_volume(mbo_surface s, void* A, int64_t n_plus, mbo_stats* stats, void* stream) {
+  if (!s || !A || ((uintptr_t)A & 15)) return MBO_ERR_INVALID_ARG;
+  if (s->n > 3) return sfail(s, MBO_ERR_UNSUPPORTED_SIZE, "%s", "the volume-preserving step supports n <= 3");
+  if (n_plus > s->nq) return sfail(s, MBO_ERR_INVALID_ARG, "%s", "n_plus exceeds the number of points");
+  const size_t elem = s->dtype == MBO_F32 ? 4 : 8;
+  const size_t fbytes = (size_t)s->C * (size_t)s->nq * elem;
+  if (!s->Au) {
+    SCK(cudaMalloc(&s->Au, fbytes));
+    SCK(cudaMalloc((void**)&s->vkeys, (size_t)s->nq * sizeof(unsigned long long)));
+    SCK(cudaMalloc((void**)&s->vss, sizeof(SelectState)));
+    s->bytes += fbytes + (size_t)s->nq * 8 + sizeof(SelectState);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the diffused field in the caller's order; the previous field kept for the statistics
+  mbo_status rc = surface_diffusion(s, A, s->Au, true, st);
+  if (rc != MBO_OK) return rc;
+  SCK(cudaMemcpyAsync(s->At, A, fbytes, cudaMemcpyDeviceToDevice, st));
+  // dE keys, the n_plus largest by radix selection, class assignment (the
+  // kernels of the flat-torus volume step, on the nq points)
+  Geom g{};
+  g.P = s->nq;
+  g.n = s->n;
+  g.C = s->C;
+  const StatsPtrs none{};
+  const int blocks = (int)std::min<long long>((s->nq + 255) / 256, 152 * 16);
+  auto vol = [&](int which) {
+    return s->dtype == MBO_F32
+               ? launch_volume<float>(which, g, static_cast<const float*>(s->Au), static_cast<float*>(A),
+                                      s->vkeys, s->vss, none, 0.0, blocks, st)
+               : launch_volume<double>(which, g, static_cast<const double*>(s->Au), static_cast<double*>(A),
+                                       s->vkeys, s->vss, none, 0.0, blocks, st);
+  };
+  SCK(vol(0));
+  if (n_plus < 0) {
+    SCK(cudaMemsetAsync(&s->vss->n_plus, 0, sizeof(unsigned long long), st));
+    SCK(vol(1));
+  }
+  SCK(launch_select_init(s->vss, n_plus, st));
+  SCK(launch_select(s->vkeys, s->nq, s->vss, blocks, st));
+  SCK(vol(2));
+  SCK(cudaMemsetAsync(s->st, 0, sizeof(SurfStats), st));
+  const unsigned pb = (unsigned)((s->nq + kProjThreads - 1) / kProjThreads);
+#define MBO_SDELTA(T, NM)                                                                   \
+  k_sdelta<T, NM><<<pb, kProjThreads, 0, st>>>(static_cast<const T*>(s->At), static_cast<const T*>(A), s->nq, s->st)
+  if (s->dtype == MBO_F32) {
+    if (s->n == 1) MBO_SDELTA(float, 1); else if (s->n == 2) MBO_SDELTA(float, 2); else MBO_SDELTA(float, 3);
+  } else {
+    if (s->n == 1) MBO_SDELTA(double, 1); else if (s->n == 2) MBO_SDELTA(double, 2); else MBO_SDELTA(double, 3);
+  }
+#undef MBO_SDELTA
+  SCK(cudaGetLastError());
+  if (stats) {
+    SCK(cudaMemcpyAsync(s->h_st, s->st, sizeof(SurfStats), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    double md;
+    std::memcpy(&md, &s->h_st->maxd_bits, sizeof(md));
+    stats->energy = NAN;
+    stats->max_delta = md;
+    stats->det_flips = (int64_t)s->h_st->flips;
+    stats->fallback_points = 0;
+    stats->nonfinite = (int64_t)s->h_st->nonfinite;
+    if (stats->nonfinite) {
+      snprintf(s->err, sizeof(s->err), "non-finite values in the assigned field");
       return MBO_ERR_NUMERIC;
     }
   }

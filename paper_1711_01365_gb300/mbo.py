@@ -36,7 +36,8 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
 SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
                    "mbo_surface_peanut_band",
                    "mbo_surface_create", "mbo_surface_destroy", "mbo_surface_get_params",
-                   "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_profile_enable",
+                   "mbo_surface_diffuse", "mbo_surface_step", "mbo_surface_step_volume",
+                   "mbo_surface_profile_enable",
                    "mbo_surface_profile_read", "mbo_surface_workspace_bytes",
                    "mbo_surface_last_error")
 
@@ -144,6 +145,7 @@ def lib():
     L.mbo_surface_get_params.argtypes = [vp, C.POINTER(mbo_surface_params)]
     L.mbo_surface_diffuse.argtypes = [vp, vp, vp, vp]
     L.mbo_surface_step.argtypes = [vp, vp, C.POINTER(mbo_stats), vp]
+    L.mbo_surface_step_volume.argtypes = [vp, vp, C.c_int64, C.POINTER(mbo_stats), vp]
     L.mbo_surface_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_surface_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_surface_workspace_bytes.argtypes = [vp]
@@ -152,7 +154,8 @@ def lib():
     L.mbo_surface_last_error.restype = C.c_char_p
     for f in ("mbo_surface_heat_modes", "mbo_surface_sphere_band", "mbo_surface_peanut_band", "mbo_surface_create",
               "mbo_surface_destroy", "mbo_surface_get_params", "mbo_surface_diffuse",
-              "mbo_surface_step", "mbo_surface_profile_enable", "mbo_surface_profile_read"):
+              "mbo_surface_step", "mbo_surface_step_volume", "mbo_surface_profile_enable",
+              "mbo_surface_profile_read"):
         getattr(L, f).restype = C.c_int
     for f in ("mbo_create", "mbo_destroy", "mbo_diffuse", "mbo_project", "mbo_step", "mbo_lyapunov",
               "mbo_run_until_stationary", "mbo_profile_enable", "mbo_profile_read",
@@ -515,6 +518,13 @@ def mbo_surface_step(s, A, want_stats: bool = False, stream=None):
     return st.as_dict() if want_stats else None
 
 
+def mbo_surface_step_volume(s, A, n_plus: int = -1, want_stats: bool = False, stream=None):
+    st = mbo_stats()
+    _scheck(lib().mbo_surface_step_volume(s, _ptr(A), int(n_plus), C.byref(st) if want_stats else None,
+                                          _stream(stream)), s)
+    return st.as_dict() if want_stats else None
+
+
 def mbo_surface_profile_enable(s, enable: bool = True) -> None:
     _scheck(lib().mbo_surface_profile_enable(s, 1 if enable else 0), s)
 
@@ -561,3 +571,6 @@ class Surface:
 
     def step(self, A, want_stats=False, stream=None):
         return mbo_surface_step(self.h, A, want_stats, stream)
+
+    def step_volume(self, A, n_plus: int = -1, want_stats=False, stream=None):
+        return mbo_surface_step_volume(self.h, A, n_plus, want_stats, stream)

@@ -11,6 +11,8 @@ GPU against the oracle (oracle/surface.py).
   last block) and on a coarse sphere band.
 * Step: the projected field equals the oracle's step where the class is
   unambiguous, and is orthogonal everywhere.
+* Volume-preserving step (Sec. 7 on the surface): the SO(n) count is exact and
+  the values match the oracle's step away from the selection threshold.
 * Full size (the sphere experiment of Sec. 6.2: dx = 0.05, tau = 0.005,
   eps = 1e-6, p = 3): properties that hold at any size -- constants are kept,
   the degree-1 harmonic z decays by 1 - 2 tau (Laplace-Beltrami, first order
@@ -233,4 +235,54 @@ def test_runtime_width_fp32(M):
     torch.cuda.synchronize()
     ref = S.surface_diffuse(A, xq, wq, xc, tau, p["h"], p["M"])
     assert np.abs(out.double().cpu().numpy() - ref).max() <= 1e-3 * max(1.0, np.abs(ref).max())
+    s.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_volume_step_matches_the_oracle(M, n, dtype):
+    """Sec. 7 on a surface: the GPU's volume-preserving step (dE keys, radix
+    selection, class assignment) against the oracle's at three counts: the
+    SO(n) count is exact, and away from the selection threshold (where a
+    diffusion difference cannot reorder dE) the values match to the step
+    tolerance (first-order conditioning bound)."""
+    nq, tau, eps = 2001, 0.01, EPS[dtype]
+    xq, wq, xc = clustered(nq, 60 + n)
+    A = field(n, nq, 70 + n)
+    n0 = O.count_positive(A, n)
+    s = M.Surface(xq, wq, xc, n, tau, eps, dtype)
+    p = s.params()
+    for n_plus in (-1, max(n0 - nq // 7, 0), min(n0 + nq // 5, nq)):
+        ref, Ato, dE, sto = S.surface_step_volume(A, xq, wq, xc, n, tau, p["h"], p["M"], n_plus)
+        k = sto["n_plus"]
+        a = torch.tensor(A, dtype=_tdt(dtype), device="cuda")
+        st = s.step_volume(a, n_plus, want_stats=True)
+        B = a.double().cpu().numpy()
+        d = np.linalg.det(_mats(B, n))
+        assert int((d > 0).sum()) == k
+        order = np.sort(dE)[::-1]
+        lam_hi = order[k - 1] if k > 0 else np.inf
+        lam_lo = order[k] if k < nq else -np.inf
+        scale = max(1.0, np.abs(Ato).max())
+        margin = 1e-3 * scale if dtype == "f32" else 1e-4 * scale
+        far = (np.abs(dE - lam_hi) > margin) & (np.abs(dE - lam_lo) > margin)
+        sv = np.linalg.svd(_mats(Ato, n), compute_uv=False)
+        cs = sv[:, -1] + (sv[:, -2] if n > 1 else sv[:, -1])
+        well = far & (cs >= 0.05 * scale)
+        assert well.sum() > nq // 4
+        err = np.abs(B - ref).max(axis=0)
+        assert np.all(err[well] <= 2 * n * TOL[dtype] * scale / cs[well] + (2e-5 if dtype == "f32" else 1e-10))
+        assert st["det_flips"] == sto["det_flips"] or not far.all()
+        Bm = _mats(B, n)
+        assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < (2e-6 if dtype == "f32" else 1e-12)
+    s.close()
+
+
+def test_volume_step_order4_unsupported(M):
+    xq, wq, xc = clustered(64, 3)
+    s = M.Surface(xq, wq, xc, 4, 0.01, 1e-6, "f32")
+    a = torch.zeros((16, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(M.MboError) as ei:
+        s.step_volume(a, 10)
+    assert ei.value.status == 2
     s.close()
