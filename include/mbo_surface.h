@@ -125,16 +125,19 @@ MBO_API mbo_status mbo_surface_diffuse(mbo_surface s, const void* A, void* A_til
  * energy is NaN (the surface path defines no Lyapunov value). */
 MBO_API mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stream);
 
-/* One volume-preserving step on the surface (Sec. 7 with the diffusion above),
- * in place: the n_plus points of largest dE = <T+ - T-, A~> (T+, T- the
- * closest matrices of SO(n) and SO^-(n) to the diffused A~, Lemma 7.1) take
- * T+, the others T- (Lemma 7.2 with one unit of volume per point; equal dE:
- * lower point index first).  n_plus < 0: the number of points with
- * det A > 0 in the input, so that repeated steps keep the count.  n <= 3
- * (MBO_ERR_UNSUPPORTED_SIZE otherwise); n_plus > nq is MBO_ERR_INVALID_ARG.
- * stats as in mbo_surface_step (fallback_points 0).  Allocates 2 n*n nq
- * elements and nq keys on first use. */
-MBO_API mbo_status mbo_surface_step_volume(mbo_surface s, void* A, int64_t n_plus, mbo_stats* stats,
+/* One volume-preserving step on the surface (Sec. 7, Algorithm 3), in place.
+ * After the diffusion above, every point gets dE = <T+ - T-, A~> (T+, T- the
+ * closest matrices of SO(n) and SO^-(n) to the diffused A~, Lemma 7.1).  Taking
+ * points in decreasing dE (equal dE: lower point index first) and adding their
+ * weights w_q (the plan's quadrature weights: each point's share of the band
+ * volume), the smallest prefix whose weight reaches `volume` takes T+ and the
+ * other points take T- (Algorithm 3; Lemma 7.2).  volume < 0: the weight of the
+ * points with det A > 0 in the input, so that repeated steps keep it.  Weights
+ * are summed exactly in fixed point (w_q scaled so that all sum to 2^62).
+ * n <= 3 (MBO_ERR_UNSUPPORTED_SIZE otherwise); negative weights or a NaN volume
+ * are MBO_ERR_INVALID_ARG.  stats as in mbo_surface_step (fallback_points 0).
+ * Allocates 2 n*n nq elements and 2 nq 64-bit words on first use. */
+MBO_API mbo_status mbo_surface_step_volume(mbo_surface s, void* A, double volume, mbo_stats* stats,
                                            void* stream);
 
 /* Per-pass device timing of the surface calls (CUDA events around each

@@ -323,26 +323,34 @@ def surface_step(A: np.ndarray, xs: np.ndarray, ws: np.ndarray, xt: np.ndarray, 
 # --- volume-preserving step on the surface (Sec. 7 on a closed surface) ---------
 
 def surface_step_volume(A: np.ndarray, xs: np.ndarray, ws: np.ndarray, xt: np.ndarray, n: int,
-                        tau: float, h: float, M: int, n_plus: int = -1):
-    """One volume-preserving step (Sec. 7) with the surface diffusion of
-    Algorithm 2: A~ = surface_diffuse(A); dE(x) = <T+(A~) - T-(A~), A~> per
-    point (T+/T- the closest matrices of SO(n) / SO^-(n), Lemma 7.1); the n_plus
-    points of largest dE (equal dE: lower point index first) take T+, the rest
-    T- (Lemma 7.2 with one unit of volume per point, the threshold form of
-    Algorithm 3).  n_plus < 0: the number of points with det A > 0.  Returns
-    (A_next, A~, dE, stats)."""
+                        tau: float, h: float, M: int, volume: float = -1.0, weights=None):
+    """One volume-preserving step on the surface (Sec. 7, Algorithm 3) with the
+    diffusion of Algorithm 2: A~ = surface_diffuse(A); dE(x) = <T+(A~) - T-(A~), A~>
+    per point (T+/T- the closest matrices of SO(n) / SO^-(n), Lemma 7.1).  Points
+    are taken in decreasing dE (equal dE: lower index first), adding their
+    weights (default: the quadrature weights ws) until the total reaches the
+    volume V; those take T+, the rest T-.  volume < 0: V is the weight of the
+    points with det A > 0.  Weights are added in exact rational arithmetic.
+    Returns (A_next, A~, dE, stats)."""
+    from fractions import Fraction
     A0 = np.asarray(A, dtype=np.float64)
+    w = np.asarray(ws if weights is None else weights, dtype=np.float64)
     At = surface_diffuse(A0, xs, ws, xt, tau, h, M)
     npt = At.shape[1]
     mats = At.T.reshape(npt, n, n)
     dE = np.array([_core.delta_energy(m) for m in mats])
-    if n_plus < 0:
-        n_plus = _core.count_positive(A0, n)
+    d0 = np.array([np.linalg.det(A0[:, i].reshape(n, n)) for i in range(npt)])
+    wf = [Fraction(float(x)) for x in w]
+    V = sum((wf[i] for i in range(npt) if d0[i] > 0), Fraction(0)) if volume < 0 else Fraction(float(volume))
     order = np.lexsort((np.arange(npt), -dE))
     plus = np.zeros(npt, dtype=bool)
-    plus[order[:n_plus]] = True
+    V0 = Fraction(0)
+    for i in order:
+        if V0 >= V:
+            break
+        plus[i] = True
+        V0 += wf[i]
     B = np.stack([_core.polar_class(m, 1 if p else -1).reshape(-1) for m, p in zip(mats, plus)], axis=1)
-    d0 = np.array([np.linalg.det(A0[:, i].reshape(n, n)) for i in range(npt)])
     stats = {"max_delta": float(np.abs(B - A0).max()), "det_flips": int(np.sum((d0 > 0) != plus)),
-             "n_plus": int(n_plus)}
+             "selected": int(plus.sum()), "volume": float(V), "selected_volume": float(V0)}
     return B, At, dE, stats

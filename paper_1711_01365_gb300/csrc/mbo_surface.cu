@@ -427,6 +427,123 @@ __global__ void __launch_bounds__(kProjThreads) k_sdelta(const T* old, const T* 
   }
 }
 
+// Weighted selection of Algorithm 3 (Sec. 7 on surfaces): with points ordered
+// by decreasing dE (ascending key, lower index first on equal keys), the
+// smallest prefix whose weight reaches the target volume V.  Weights are
+// fixed-point integers (the plan scales every w_q so that all of them sum to
+// 2^62), so the sums are exact and independent of the summation order.  Twelve
+// MSB-first passes over 8-bit digits of the 96-bit (key, index) composite, as
+// in the count-based selection, with weight sums per digit instead of counts;
+// the result goes into a SelectState for the class assignment (a point takes
+// SO(n) iff its (key, index) <= (hi, lo) and the target is positive).
+struct WSelect {
+  unsigned long long hi;      // key part of the prefix / result
+  unsigned int lo;            // index part
+  int all;                    // the target exceeds the total weight: select every point
+  unsigned long long vrem;    // weight still to reach inside the current prefix
+  unsigned long long target;  // V
+  unsigned long long hist[256];
+};
+
+__device__ __forceinline__ unsigned wdigit(unsigned long long key, unsigned idx, int d) {
+  return d < 8 ? (unsigned)((key >> (56 - 8 * d)) & 0xffu) : ((idx >> (24 - 8 * (d - 8))) & 0xffu);
+}
+
+__device__ __forceinline__ bool wprefix(unsigned long long key, unsigned idx, unsigned long long hi,
+                                        unsigned lo, int d) {
+  if (d == 0) return true;
+  if (d <= 8) {
+    const int sh = 64 - 8 * d;
+    return (key >> sh) == (hi >> sh);
+  }
+  if (key != hi) return false;
+  const int sh = 32 - 8 * (d - 8);
+  return (idx >> sh) == (lo >> sh);
+}
+
+// V = the weight of the points with det A > 0 (the input's own volume).
+template <typename T, int NM>
+__global__ void __launch_bounds__(256) k_wvolume(const T* A, const unsigned long long* w, long long nq,
+                                                 WSelect* ws) {
+  constexpr int C = NM * NM;
+  __shared__ unsigned long long part[8];
+  unsigned long long v = 0;
+  for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nq; q += (long long)gridDim.x * 256) {
+    T m[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) m[c] = A[c * nq + q];
+    if (det_sign<NM>(m) > T(0)) v += w[q];
+  }
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < 8; ++i) t += part[i];
+    atomicAdd(&ws->target, t);
+  }
+}
+
+__global__ void k_wselect_init(WSelect* ws, unsigned long long target, int use_given) {
+  if (threadIdx.x == 0) {
+    if (use_given) ws->target = target;
+    ws->hi = 0;
+    ws->lo = 0;
+    ws->all = 0;
+    ws->vrem = ws->target;
+  }
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) ws->hist[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_wselect_hist(const unsigned long long* __restrict__ keys,
+                                                      const unsigned long long* __restrict__ w, long long nq,
+                                                      WSelect* ws, int d) {
+  __shared__ unsigned long long h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const unsigned long long hi = ws->hi;
+  const unsigned lo = ws->lo;
+  const bool active = ws->target > 0 && !ws->all;
+  if (active) {
+    for (long long x = blockIdx.x * 256LL + threadIdx.x; x < nq; x += (long long)gridDim.x * 256) {
+      const unsigned long long key = keys[x];
+      if (wprefix(key, (unsigned)x, hi, lo, d)) atomicAdd(&h[wdigit(key, (unsigned)x, d)], w[x]);
+    }
+  }
+  __syncthreads();
+  if (active)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+      if (h[i]) atomicAdd(&ws->hist[i], h[i]);
+}
+
+__global__ void k_wselect_pick(WSelect* ws, SelectState* ss, int d) {
+  if (threadIdx.x != 0) return;
+  if (ws->target > 0 && !ws->all) {
+    const unsigned long long v = ws->vrem;
+    unsigned long long cum = 0;
+    int b = 0;
+    for (; b < 256; ++b) {
+      if (cum + ws->hist[b] >= v) break;
+      cum += ws->hist[b];
+    }
+    if (b == 256) {  // only on the first pass: V exceeds the total weight
+      ws->all = 1;
+      ws->hi = ~0ull;
+      ws->lo = ~0u;
+    } else {
+      ws->vrem = v - cum;
+      if (d < 8) ws->hi |= ((unsigned long long)b) << (56 - 8 * d);
+      else ws->lo |= ((unsigned)b) << (24 - 8 * (d - 8));
+    }
+  }
+  for (int i = 0; i < 256; ++i) ws->hist[i] = 0;
+  if (d == 11) {
+    ss->hi = ws->hi;
+    ss->lo = ws->lo;
+    ss->n_plus = ws->target > 0 ? 1 : 0;
+  }
+}
+
 // ----------------------------------------------------------------------------
 // host-side geometry (Algorithm 2, step 1) and plan parameters
 // ----------------------------------------------------------------------------
@@ -594,6 +711,10 @@ struct mbo_surface_ctx {
   void* Au = nullptr;                      // diffused values in the caller's order, C x nq
   unsigned long long* vkeys = nullptr;     // one selection key per point
   SelectState* vss = nullptr;
+  WSelect* vws = nullptr;
+  unsigned long long* vw = nullptr;        // fixed-point weights (caller's order), sum 2^62
+  double wscale = 0;                       // fixed-point units per unit of w_q
+  std::vector<double> hw;                  // the weights w_q (host copy)
   void* su = nullptr;         // V4<T> sources
   int* sidx = nullptr;
   int* gsrc = nullptr;
@@ -868,7 +989,7 @@ mbo_status mbo_surface_destroy(mbo_surface s) {
   cudaDeviceSynchronize();
   if (s->fine) mbo_destroy(s->fine);
   void* bufs[] = {s->F, s->At, s->su, s->sidx, s->gsrc, s->gt0, s->bgrp, s->bid,
-                  s->tu, s->tidx, s->tgrp, s->tg0, s->st, s->Au, s->vkeys, s->vss};
+                  s->tu, s->tidx, s->tgrp, s->tg0, s->st, s->Au, s->vkeys, s->vss, s->vws, s->vw};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->h_st) cudaFreeHost(s->h_st);
@@ -902,6 +1023,7 @@ mbo_status mbo_surface_create(mbo_surface* out, int64_t nq, const double* xq, co
   s->nq = nq;
   s->tau = tau;
   s->eps = eps;
+  s->hw.assign(wq, wq + nq);
   mbo_surface_params& prm = s->prm;
 
   // extent and centre of all points
@@ -1134,25 +1256,37 @@ mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, void* stre
   return MBO_OK;
 }
 
-mbo_status mbo_surface_step_volume(mbo_surface s, void* A, int64_t n_plus, mbo_stats* stats, void* stream) {
-  if (!s || !A || ((uintptr_t)A & 15)) return MBO_ERR_INVALID_ARG;
+mbo_status mbo_surface_step_volume(mbo_surface s, void* A, double volume, mbo_stats* stats, void* stream) {
+  if (!s || !A || ((uintptr_t)A & 15) || std::isnan(volume)) return MBO_ERR_INVALID_ARG;
   if (s->n > 3) return sfail(s, MBO_ERR_UNSUPPORTED_SIZE, "%s", "the volume-preserving step supports n <= 3");
-  if (n_plus > s->nq) return sfail(s, MBO_ERR_INVALID_ARG, "%s", "n_plus exceeds the number of points");
   const size_t elem = s->dtype == MBO_F32 ? 4 : 8;
   const size_t fbytes = (size_t)s->C * (size_t)s->nq * elem;
   if (!s->Au) {
+    // fixed-point weights: w_q scaled so that all of them sum to 2^62
+    long double tot = 0;
+    for (double w : s->hw) {
+      if (!(w >= 0)) return sfail(s, MBO_ERR_INVALID_ARG, "%s", "the volume step needs weights w_q >= 0");
+      tot += w;
+    }
+    if (!(tot > 0)) return sfail(s, MBO_ERR_INVALID_ARG, "%s", "the volume step needs a positive total weight");
+    s->wscale = (double)(std::ldexp(1.0L, 62) / tot);
+    std::vector<unsigned long long> wf(s->nq);
+    for (long long q = 0; q < s->nq; ++q) wf[q] = (unsigned long long)((long double)s->hw[q] * s->wscale);
     SCK(cudaMalloc(&s->Au, fbytes));
     SCK(cudaMalloc((void**)&s->vkeys, (size_t)s->nq * sizeof(unsigned long long)));
     SCK(cudaMalloc((void**)&s->vss, sizeof(SelectState)));
-    s->bytes += fbytes + (size_t)s->nq * 8 + sizeof(SelectState);
+    SCK(cudaMalloc((void**)&s->vws, sizeof(WSelect)));
+    SCK(cudaMalloc((void**)&s->vw, (size_t)s->nq * sizeof(unsigned long long)));
+    SCK(cudaMemcpy(s->vw, wf.data(), (size_t)s->nq * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    s->bytes += fbytes + (size_t)s->nq * 16 + sizeof(SelectState) + sizeof(WSelect);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the diffused field in the caller's order; the previous field kept for the statistics
   mbo_status rc = surface_diffusion(s, A, s->Au, true, st);
   if (rc != MBO_OK) return rc;
   SCK(cudaMemcpyAsync(s->At, A, fbytes, cudaMemcpyDeviceToDevice, st));
-  // dE keys, the n_plus largest by radix selection, class assignment (the
-  // kernels of the flat-torus volume step, on the nq points)
+  // dE keys (the flat-torus volume step's kernels, on the nq points), the
+  // weighted selection of Algorithm 3, class assignment
   Geom g{};
   g.P = s->nq;
   g.n = s->n;
@@ -1167,12 +1301,26 @@ mbo_status mbo_surface_step_volume(mbo_surface s, void* A, int64_t n_plus, mbo_s
                                        s->vkeys, s->vss, none, 0.0, blocks, st);
   };
   SCK(vol(0));
-  if (n_plus < 0) {
-    SCK(cudaMemsetAsync(&s->vss->n_plus, 0, sizeof(unsigned long long), st));
-    SCK(vol(1));
+  if (volume < 0) {
+    SCK(cudaMemsetAsync(&s->vws->target, 0, sizeof(unsigned long long), st));
+#define MBO_WVOL(T, NM)                                                                              \
+  k_wvolume<T, NM><<<blocks, 256, 0, st>>>(static_cast<const T*>(A), s->vw, s->nq, s->vws)
+    if (s->dtype == MBO_F32) {
+      if (s->n == 1) MBO_WVOL(float, 1); else if (s->n == 2) MBO_WVOL(float, 2); else MBO_WVOL(float, 3);
+    } else {
+      if (s->n == 1) MBO_WVOL(double, 1); else if (s->n == 2) MBO_WVOL(double, 2); else MBO_WVOL(double, 3);
+    }
+#undef MBO_WVOL
+    k_wselect_init<<<1, 256, 0, st>>>(s->vws, 0, 0);
+  } else {
+    const long double t = std::min((long double)volume * s->wscale, std::ldexp(1.0L, 63));
+    k_wselect_init<<<1, 256, 0, st>>>(s->vws, (unsigned long long)std::llround((double)t), 1);
   }
-  SCK(launch_select_init(s->vss, n_plus, st));
-  SCK(launch_select(s->vkeys, s->nq, s->vss, blocks, st));
+  for (int d = 0; d < 12; ++d) {
+    k_wselect_hist<<<blocks, 256, 0, st>>>(s->vkeys, s->vw, s->nq, s->vws, d);
+    k_wselect_pick<<<1, 32, 0, st>>>(s->vws, s->vss, d);
+  }
+  SCK(cudaGetLastError());
   SCK(vol(2));
   SCK(cudaMemsetAsync(s->st, 0, sizeof(SurfStats), st));
   const unsigned pb = (unsigned)((s->nq + kProjThreads - 1) / kProjThreads);

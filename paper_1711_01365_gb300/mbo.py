@@ -145,7 +145,7 @@ def lib():
     L.mbo_surface_get_params.argtypes = [vp, C.POINTER(mbo_surface_params)]
     L.mbo_surface_diffuse.argtypes = [vp, vp, vp, vp]
     L.mbo_surface_step.argtypes = [vp, vp, C.POINTER(mbo_stats), vp]
-    L.mbo_surface_step_volume.argtypes = [vp, vp, C.c_int64, C.POINTER(mbo_stats), vp]
+    L.mbo_surface_step_volume.argtypes = [vp, vp, C.c_double, C.POINTER(mbo_stats), vp]
     L.mbo_surface_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_surface_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_surface_workspace_bytes.argtypes = [vp]
@@ -518,9 +518,9 @@ def mbo_surface_step(s, A, want_stats: bool = False, stream=None):
     return st.as_dict() if want_stats else None
 
 
-def mbo_surface_step_volume(s, A, n_plus: int = -1, want_stats: bool = False, stream=None):
+def mbo_surface_step_volume(s, A, volume: float = -1.0, want_stats: bool = False, stream=None):
     st = mbo_stats()
-    _scheck(lib().mbo_surface_step_volume(s, _ptr(A), int(n_plus), C.byref(st) if want_stats else None,
+    _scheck(lib().mbo_surface_step_volume(s, _ptr(A), float(volume), C.byref(st) if want_stats else None,
                                           _stream(stream)), s)
     return st.as_dict() if want_stats else None
 
@@ -572,5 +572,5 @@ class Surface:
     def step(self, A, want_stats=False, stream=None):
         return mbo_surface_step(self.h, A, want_stats, stream)
 
-    def step_volume(self, A, n_plus: int = -1, want_stats=False, stream=None):
-        return mbo_surface_step_volume(self.h, A, n_plus, want_stats, stream)
+    def step_volume(self, A, volume: float = -1.0, want_stats=False, stream=None):
+        return mbo_surface_step_volume(self.h, A, volume, want_stats, stream)

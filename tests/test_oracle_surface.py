@@ -256,29 +256,46 @@ def _small_surface_case(npts, seed, n):
 
 @pytest.mark.parametrize("n", [2, 3])
 def test_surface_volume_step_is_the_constrained_optimum(n):
-    """Sec. 7, Lemma 7.2: with one unit of volume per point the selection
-    maximises sum <T_class(x), A~(x)> over all assignments with n_plus points in
-    SO(n) (brute force over every subset of a tiny point set), keeps that count,
-    and equals the plain step when n_plus is the plain step's own count."""
+    """Sec. 7, Algorithm 3 and Lemma 7.2 on a surface: the selected set (a
+    prefix in decreasing dE reaching the volume V) maximises sum w (dE - lam)
+    over all subsets, lam its smallest dE (brute force over all subsets of a
+    tiny point set), reaches V with a minimal prefix, reduces to the counting form for
+    equal weights, and equals the plain step when V is the plain step's own
+    volume."""
     import itertools
-    A, xs, ws, xt, h, M = _small_surface_case(10, 40 + n, n)
-    B, At, dE, st = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, n_plus=4)
+    A, xs, ws, xt, h, M = _small_surface_case(11, 40 + n, n)
+    g = np.random.default_rng(90 + n)
+    w = g.uniform(0.2, 1.0, 11)
+    V = 0.45 * w.sum()
+    B, At, dE, st = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, volume=V, weights=w)
     mats = At.T.reshape(-1, n, n)
     tp = np.stack([O.polar_class(m, 1).reshape(-1) for m in mats], 1)
     tm = np.stack([O.polar_class(m, -1).reshape(-1) for m in mats], 1)
     gain = (tp * At).sum(0) - (tm * At).sum(0)
     assert np.allclose(gain, dE, atol=1e-12)
-    best = max(sum(gain[list(c)]) for c in itertools.combinations(range(10), 4))
-    sel = np.array([np.linalg.det(B[:, i].reshape(n, n)) > 0 for i in range(10)])
-    assert sel.sum() == 4
-    assert gain[sel].sum() == pytest.approx(best, abs=1e-12)
+    sel = np.array([np.linalg.det(B[:, i].reshape(n, n)) > 0 for i in range(11)])
+    Wsel = w[sel].sum()
+    assert Wsel >= V and Wsel - w[sel][np.argmin(dE[sel])] < V
+    # Lemma 7.2's form: the set maximises sum w (dE - lam) over all subsets, lam its smallest dE
+    lam = dE[sel].min()
+    best = max(sum(w[list(c)] * (dE[list(c)] - lam)) for r in range(12)
+               for c in itertools.combinations(range(11), r))
+    assert (w[sel] * (dE[sel] - lam)).sum() == pytest.approx(best, abs=1e-12)
     Bm = B.T.reshape(-1, n, n)
     assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < 1e-12
-    # the plain step's own count reproduces the plain step
+    # equal weights: the n_plus largest dE
+    Be, _, _, ste = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, volume=4.0, weights=np.ones(11))
+    assert ste["selected"] == 4
+    top = np.lexsort((np.arange(11), -dE))[:4]
+    assert set(np.flatnonzero([np.linalg.det(Be[:, i].reshape(n, n)) > 0 for i in range(11)])) == set(top)
+    # the plain step's own volume reproduces the plain step
     Bp, _, _ = S.surface_step(A, xs, ws, xt, n, 0.02, h, M)
-    k = int(sum(np.linalg.det(Bp[:, i].reshape(n, n)) > 0 for i in range(10)))
-    Bv, _, _, _ = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, n_plus=k)
+    pos = np.array([np.linalg.det(Bp[:, i].reshape(n, n)) > 0 for i in range(11)])
+    # (a volume just below the set's weight: the minimal prefix reaching it is that set)
+    Bv, _, _, _ = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, volume=w[pos].sum() * (1 - 1e-12),
+                                        weights=w)
     assert np.abs(Bv - Bp).max() < 1e-12
-    # n_plus < 0 keeps the input's count
-    _, _, _, st2 = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M)
-    assert st2["n_plus"] == O.count_positive(A, n)
+    # volume < 0 keeps the input's
+    _, _, _, st2 = S.surface_step_volume(A, xs, ws, xt, n, 0.02, h, M, weights=w)
+    d0 = np.array([np.linalg.det(A[:, i].reshape(n, n)) for i in range(11)])
+    assert st2["volume"] == pytest.approx(w[d0 > 0].sum(), rel=1e-15)
