@@ -131,8 +131,11 @@ MBO_API mbo_status mbo_surface_step(mbo_surface s, void* A, mbo_stats* stats, vo
  * points in decreasing dE (equal dE: lower point index first) and adding their
  * weights w_q (the plan's quadrature weights: each point's share of the band
  * volume), the smallest prefix whose weight reaches `volume` takes T+ and the
- * other points take T- (Algorithm 3; Lemma 7.2).  volume < 0: the weight of the
- * points with det A > 0 in the input, so that repeated steps keep it.  Weights
+ * other points take T- (Algorithm 3; Lemma 7.2), so the selected weight lies in
+ * [volume, volume + the last point's weight).  volume < 0: the weight of the
+ * points with det A > 0 in the input; repeated calls in that mode may then
+ * gain up to one point's weight per step, so a run that must keep its volume
+ * passes the same volume to every step.  Weights
  * are summed exactly in fixed point (w_q scaled so that all sum to 2^62).
  * n <= 3 (MBO_ERR_UNSUPPORTED_SIZE otherwise); negative weights or a NaN volume
  * are MBO_ERR_INVALID_ARG.  stats as in mbo_surface_step (fallback_points 0).
