@@ -565,6 +565,17 @@ def run_surface(args, ws, rank, local):
     ms = e0.elapsed_time(e1)
     passes = M.mbo_surface_profile_read(s.h)
     M.mbo_surface_profile_enable(s.h, False)
+    # the volume-preserving step (Sec. 7, Algorithm 3) on the same field, volume of its own input
+    for _ in range(2):
+        s.step_volume(A, -1.0)
+    barrier()
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    for _ in range(args.steps):
+        s.step_volume(A, -1.0)
+    v1.record(stream)
+    barrier()
+    vol_ms = v0.elapsed_time(v1) / args.steps
     value, t = job_throughput(nq, args.steps, ms / 1e3, device="cuda")
     # spreading: W^3 multiply-adds per source and channel (2 flops each) on the
     # FP32 vector units: 152 SMs x 128 lanes x 2 flops x the SM clock
@@ -593,7 +604,9 @@ def run_surface(args, ws, rank, local):
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": None, "e2e": None,
                 "gpu_launches": 8 * args.steps, "clocks": clocks,
-                "note": "secondary workload; cpu_baseline and e2e are measured on the 1024^2 headline only"}
+                "volume_step_ms": vol_ms,
+                "note": "secondary workload; cpu_baseline and e2e are measured on the 1024^2 headline only; "
+                        "volume_step_ms: mbo_surface_step_volume on the same field, timed after the main steps"}
         print(json.dumps(line), flush=True)
     s.close()
 
