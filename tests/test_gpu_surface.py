@@ -293,3 +293,31 @@ def test_volume_step_order4_unsupported(M):
         s.step_volume(a, 10)
     assert ei.value.status == 2
     s.close()
+
+
+@pytest.mark.parametrize("case", ["single", "coincident"])
+def test_degenerate_point_sets(M, case):
+    """A single point (zero extent: the plan takes R = 1) and 50 copies of one
+    point with its closest point (one footprint group, one bin): the diffusion
+    equals the oracle's double sum with the plan's h and M, and a step stays
+    orthogonal."""
+    n, tau, eps = 3, 0.01, 1e-6
+    if case == "single":
+        xq, xc, wq = np.array([[0.3, -0.2, 0.5]]), np.array([[0.31, -0.18, 0.49]]), np.array([0.7])
+    else:
+        xq = np.repeat([[0.1, 0.2, 0.3]], 50, axis=0)
+        xc = np.repeat([[0.12, 0.2, 0.28]], 50, axis=0)
+        wq = np.full(50, 1.0 / 50)
+    A = field(n, len(wq), 80)
+    s = M.Surface(xq, wq, xc, n, tau, eps, "f32")
+    p = s.params()
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(a)
+    s.diffuse(a, out)
+    torch.cuda.synchronize()
+    ref = S.surface_diffuse(A, xq, wq, xc, tau, p["h"], p["M"])
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= TOL["f32"] * max(1.0, np.abs(ref).max())
+    s.step(a)
+    Bm = _mats(a.double().cpu().numpy(), n)
+    assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max() < 2e-6
+    s.close()

@@ -56,6 +56,9 @@ def test_bad_arguments_rejected(lib):
         with pytest.raises(M.MboError) as ei:
             M.mbo_surface_create(*args)
         assert ei.value.status == 1
+    with pytest.raises(M.MboError) as ei:  # no points
+        M.mbo_surface_create(np.zeros((0, 3)), np.zeros(0), np.zeros((0, 3)), 2, 0.01, 1e-6)
+    assert ei.value.status == 1
     bad = pts.copy()
     bad[1, 2] = np.nan
     with pytest.raises(M.MboError) as ei:
