@@ -19,17 +19,20 @@
 //              around its coordinate.
 //   k_sproject projection of every target (Lemma 1.1) with the step statistics.
 // win(k) = 1 for |k| < M, 1/2 at |k| = M (the real part of the sum over
-// -M..M-1), 0 beyond.
+// -M..M-1), 0 beyond.  The volume-preserving step (Sec. 7, Algorithm 3) runs
+// the diffusion into the caller's point order, the flat-torus dE keys and
+// class assignment (k_vp_delta / k_vp_assign) on the points, and between them
+// a weighted radix selection (k_wselect_*).
 //
-// Points that share their nearest grid point share their footprint (the W^3
-// points spread to or read from), and the plan sorts them into such groups
-// once (the geometry is fixed).  Spreading: one warp per group, a lane per
-// footprint column (x, y) holding the W points along z for CG channels in
-// registers; the group's sources are summed there and added once to a
-// shared-memory tile of the group's bin of kBin^3 cells, which goes to the
-// grid at the end.  Interpolation: one block per group stages the footprint
-// values in shared memory once and evaluates every target of the group from
-// them, a thread per target.
+// Points whose footprints (the W^3 grid points spread to or read from) start
+// at the same grid point share their footprint, and the plan sorts them into
+// such groups once (the geometry is fixed).  Spreading: one warp per group of
+// sources, a lane per footprint column (x, y) holding the W points along z for
+// CG channels in registers; the group's sources are summed there and added once
+// to a shared-memory tile of the group's bin of kBin^3 cells, which goes to the
+// grid at the end.  Interpolation: one block per group of targets stages the
+// footprint values in shared memory once and evaluates every target of the
+// group from them, a thread per target.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,17 +66,6 @@ struct SurfStats {
 template <typename T> __device__ __forceinline__ T es_kernel(T z, T beta) {
   const T a = T(1) - z * z;
   return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
-}
-
-// Lane l < 3W of a warp computes the 1-D weight of footprint point l % W along
-// axis l / W for a point at distance d (grid units, per axis) past the
-// footprint's first point: phi(2 (i - d) / W).
-template <typename T>
-__device__ __forceinline__ T lane_weight(int lane, int W, T dx, T dy, T dz, T beta) {
-  if (lane >= 3 * W) return T(0);
-  const int ax = lane / W, i = lane - ax * W;
-  const T d = ax == 0 ? dx : (ax == 1 ? dy : dz);
-  return es_kernel((T(i) - d) * (T(2) / T(W)), beta);
 }
 
 template <typename T> struct SpreadArgs {
@@ -1272,12 +1264,30 @@ mbo_status mbo_surface_step_volume(mbo_surface s, void* A, double volume, mbo_st
     s->wscale = (double)(std::ldexp(1.0L, 62) / tot);
     std::vector<unsigned long long> wf(s->nq);
     for (long long q = 0; q < s->nq; ++q) wf[q] = (unsigned long long)((long double)s->hw[q] * s->wscale);
-    SCK(cudaMalloc(&s->Au, fbytes));
-    SCK(cudaMalloc((void**)&s->vkeys, (size_t)s->nq * sizeof(unsigned long long)));
-    SCK(cudaMalloc((void**)&s->vss, sizeof(SelectState)));
-    SCK(cudaMalloc((void**)&s->vws, sizeof(WSelect)));
-    SCK(cudaMalloc((void**)&s->vw, (size_t)s->nq * sizeof(unsigned long long)));
-    SCK(cudaMemcpy(s->vw, wf.data(), (size_t)s->nq * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    // all buffers or none: a failed call leaves the plan as it was
+    void* au = nullptr;
+    void* keys = nullptr;
+    void* ss = nullptr;
+    void* ws = nullptr;
+    void* w = nullptr;
+    cudaError_t e = cudaMalloc(&au, fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&keys, (size_t)s->nq * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ss, sizeof(SelectState));
+    if (e == cudaSuccess) e = cudaMalloc(&ws, sizeof(WSelect));
+    if (e == cudaSuccess) e = cudaMalloc(&w, (size_t)s->nq * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(w, wf.data(), (size_t)s->nq * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      void* bufs[] = {au, keys, ss, ws, w};
+      for (void* b : bufs)
+        if (b) cudaFree(b);
+      return sfail(s, e == cudaErrorMemoryAllocation ? MBO_ERR_OOM : MBO_ERR_CUDA, "%s", cudaGetErrorString(e));
+    }
+    s->Au = au;
+    s->vkeys = static_cast<unsigned long long*>(keys);
+    s->vss = static_cast<SelectState*>(ss);
+    s->vws = static_cast<WSelect*>(ws);
+    s->vw = static_cast<unsigned long long*>(w);
     s->bytes += fbytes + (size_t)s->nq * 16 + sizeof(SelectState) + sizeof(WSelect);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
