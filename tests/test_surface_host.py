@@ -78,3 +78,15 @@ def test_peanut_band_matches_the_oracle(lib, dx, wb, p):
     assert np.abs(xq - oq).max() < 1e-13
     assert np.abs(wq - ow).max() < 1e-15
     assert np.abs(xc - oc).max() < 1e-6
+
+
+def test_grid_beyond_2048_rejected(lib):
+    """Points 100 apart at tau = 1e-4 need M = 7713 modes per axis (the
+    heat-kernel approximation theorem), a grid far beyond 2048 points per
+    axis: the plan refuses it before touching the device."""
+    h, m = M.mbo_surface_heat_modes(1e-6, 1e-4, 100.0)
+    assert 4 * m > 2048
+    pts = np.array([[0.0, 0.0, 0.0], [100.0, 100.0, 100.0]])
+    with pytest.raises(M.MboError) as ei:
+        M.mbo_surface_create(pts, np.ones(2), pts, 2, 1e-4, 1e-6)
+    assert ei.value.status == 2
