@@ -82,6 +82,9 @@ typedef struct {
                             32 in [64, 384]; 0 = automatic.                       */
   int axis_tx;           /* x-columns per block of the y / z passes: a power of
                             two dividing Nx, at most 16; 0 = automatic.           */
+  int axis_stages;       /* MBO_F32 y / z passes of length 256..2048: tile
+                            buffers per block, 1 or 2 (2: the next tile's copy is
+                            in flight while a tile is transformed); 0 = automatic. */
 } mbo_config;
 
 /* Per-step record.  Step s maps A_{s} to A_{s+1}. */
@@ -197,10 +200,14 @@ MBO_API mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches,
  *     so nothing needs clearing; but calls that overlap on the GPU (different
  *     streams, or host threads without ordering) race on the array: order them,
  *     for example by using one stream.
- * A and A_tilde: caller-owned, 16-byte-aligned device fields (may be equal).
- * Asynchronous on stream.  Errors: MBO_ERR_INVALID_ARG (bad argument or
- * pointer), MBO_ERR_UNSUPPORTED_SIZE (axis length, or scratch too small),
- * MBO_ERR_CUDA (a launch or the address lookup failed). */
+ * A and A_tilde: caller-owned, 16-byte-aligned fields in the memory of the
+ * CURRENT device (the call runs there, with that device's copy of the array);
+ * they may be equal.  Asynchronous on stream.  Errors: MBO_ERR_INVALID_ARG
+ * (bad argument, or a pointer that is not device memory of the current
+ * device), MBO_ERR_UNSUPPORTED_SIZE (axis length, scratch too small, or row /
+ * column tiles larger than the device's shared memory per block, e.g. 2048
+ * points along x with n = 4 in MBO_F64), MBO_ERR_CUDA (a launch or the address
+ * lookup failed).  Every check runs before the first launch. */
 #define MBO_NOALLOC_SCRATCH_BYTES (64u << 20)
 MBO_API mbo_status mbo_diffuse_noalloc(int ndim, const int64_t* dims, int n, double tau,
                                        mbo_dtype dtype, const void* A, void* A_tilde,

@@ -2,97 +2,222 @@
 // of Osting & Wang, arXiv:1711.01365) for axes whose plan is the
 // warp-cooperative four-step transform (mbo_wfft.cuh).
 //
-//   k_wcol  a tile of TX adjacent columns of one plane is staged through
-//           shared memory with coalesced copies; one sequence (R groups of
-//           lanes) per column; forward transform, multiplier g(k)/P and the
+//   k_wcol  persistent: each block walks the tiles b = blockIdx.x,
+//           blockIdx.x + gridDim.x, ...; a tile is TX adjacent x-columns of
+//           one complex plane along the whole axis.  The tile arrives in
+//           shared memory by TMA (4-D tensor map over (x, y, z, plane), boxes
+//           of TX x 256 elements, swizzled), each column becomes one sequence
+//           (R groups of lanes): forward transform, multiplier g(k)/P and the
 //           energy partials of the Sec. 4 functional (Parseval form), inverse
-//           transform, all in registers.
+//           transform, all in registers; the result goes back by TMA store.
+//           With NBUF = 2 the next tile's load is in flight while a tile is
+//           transformed.
 #include "mbo_kernels.cuh"
+#include "mbo_tma.cuh"
 #include "mbo_wfft.cuh"
 #include "mbo_wshape.cuh"
 
 namespace mbo {
 namespace {
 
-// Strided-axis pass (y in 2-D; y and z in 3-D) on a tile of TX adjacent
-// x-columns of one complex plane; each column is one sequence of R groups.
-template <int MODE, int L, int TX>
-__global__ void __launch_bounds__(TX * w_r(L) * w_lq(L), wcol_minb(L, TX))
-k_wcol(Geom g, Tables<float> t, float2* W, StatsPtrs sp, int axis) {
-  constexpr int R = w_r(L), M = w_m(L), LQ = w_lq(L);
-  using F = WarpFFTR<M, LQ, R>;
-  constexpr int E = F::E, NT = TX * R * LQ, TS = TX + 1;  // tile row stride (complex)
-  constexpr int PS = R * F::RS;                          // transpose slots of one column
-  static_assert(TX * PS <= L * TS, "transpose regions must fit in the tile");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+constexpr int kBoxRows = 256;  // TMA box extent along the transformed axis (the hardware limit)
+
+template <int L, int TX> struct WcolShape {
+  static constexpr int R = w_r(L), M = w_m(L), LQ = w_lq(L);
+  using F = WarpFFTR<M, LQ, R, TwShared>;
+  static constexpr int E = F::E;
+  static constexpr int NT = TX * R * LQ;
+  static constexpr int PS = R * F::RS;  // transpose slots of one column (padded rows)
+  static constexpr int TILE = L * TX;   // tile slots (float2), dense, swizzled by TMA
+  static constexpr int BUF = (TILE > TX * PS ? TILE : TX * PS);
+  static constexpr int BUF_BYTES = ((BUF * 8 + 1023) / 1024) * 1024;
+  static constexpr int BOX = L < kBoxRows ? L : kBoxRows;
+  static constexpr int NBOX = L / BOX;
+  // 16-byte chunk swizzle of the TMA tile: span TX * 8 bytes (32, 64 or 128)
+  static constexpr int SWM = TX * 8 / 16 - 1;
+  static_assert(TX == 4 || TX == 8 || TX == 16, "tile widths 4, 8, 16");
+  static_assert((R * LQ) % 8 == 0, "the lane's swizzle term must not depend on j");
+};
+
+// Shared-memory bytes: NBUF tile buffers, the axis twiddles (L complex) and
+// the axis multiplier and 1 - g (L reals each), plus 1 KB of alignment slack.
+template <int L, int TX> constexpr size_t wcol_smem(int nbuf) {
+  using S = WcolShape<L, TX>;
+  return 1024 + (size_t)nbuf * S::BUF_BYTES + (size_t)L * 8 + (size_t)L * 8;
+}
+
+template <int MODE, int L, int TX, int NBUF>
+__global__ void __launch_bounds__(WcolShape<L, TX>::NT, wcol_minb(L, TX))
+k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtrs sp, int axis,
+       int ntiles, const char* __restrict__ pf, long long pf_bytes) {
+  using S = WcolShape<L, TX>;
+  using F = typename S::F;
+  constexpr int R = S::R, M = S::M, LQ = S::LQ, E = S::E, NT = S::NT, PS = S::PS;
+  extern __shared__ unsigned char smem_raw[];
   __shared__ double redd[32];
   __shared__ int s_flag;
+  __shared__ __align__(8) unsigned long long bar[NBUF];
   if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
 
-  float2* tile = reinterpret_cast<float2*>(smem_raw);
-  const long long es = (axis == 1) ? (long long)g.nx : (long long)g.nx * g.ny;
-  const int nouter = (axis == 1) ? g.nz : g.ny;
-  const long long ostride = (axis == 1) ? (long long)g.nx * g.ny : (long long)g.nx;
-  int q, o, x0;
-  col_tile(g, nouter, TX, blockIdx.x, q, o, x0);
-  float2* base = W + (long long)q * g.P + (long long)o * ostride + x0;
+  // 1024-byte aligned tile buffers (the TMA swizzle works on address bits
+  // 4..9); offsetting the shared array itself keeps every access below a
+  // shared-memory instruction
+  unsigned char* al = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float2* s_tw = reinterpret_cast<float2*>(al + NBUF * S::BUF_BYTES);
+  float* s_g = reinterpret_cast<float*>(s_tw + L);
+  float* s_om = s_g + L;
+
   const int tid = threadIdx.x;
   const int grp = tid / LQ, l = tid - grp * LQ;
   const int c = grp / R, r = grp - c * R;
-  const float2* tw = static_cast<const float2*>(t.tw[axis]);
-  const float2* twr = tw + M;
+  const int nouter = (axis == 1) ? g.nz : g.ny;
 
-  for (int i = tid; i < L * TX; i += NT) {
-    const int p = i / TX, cc = i - p * TX;
-    cp_async_elem(&tile[p * TS + cc], base + (long long)p * es + cc);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  float2 v[E];
+  // tile b of this pass: plane q, outer index o, first column x0
+  auto coords = [&](int b, int& q, int& o, int& x0) { col_tile(g, nouter, TX, b, q, o, x0); };
+  auto issue_load = [&](int b, int buf) {  // thread 0 only
+    int q, o, x0;
+    coords(b, q, o, x0);
+    float2* dst = reinterpret_cast<float2*>(al + buf * S::BUF_BYTES);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[buf], (unsigned)(S::TILE * 8));
 #pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = tile[(R * (l + LQ * j) + r) * TS + c];
-  __syncthreads();
-  float2* cbase = tile + c * PS;
-  if (MODE != AXIS_INV) F::fwd(v, cbase, r, tw, twr, l);
-  float acc = 0.f;
-  if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
-    // the last axis applies g(k) = g_x g_y (g_z); in 3-D the y frequency is
-    // the outer index o of this tile (the y pass ran before).
-    float go = 1.f, omo = 0.f;
-    if (g.ndim == 3) {
-      go = t.g[1][o];
-      omo = t.om[1][o];
+    for (int bx = 0; bx < S::NBOX; ++bx) {
+      if (axis == 1) tma_load_4d(dst + bx * S::BOX * TX, &tm, x0, bx * S::BOX, o, q, &bar[buf]);
+      else tma_load_4d(dst + bx * S::BOX * TX, &tm, x0, o, bx * S::BOX, q, &bar[buf]);
     }
-    const float* gL = t.g[axis];
-    const float* omL = t.om[axis];
-    const int x = x0 + c;
-    const float gxx = t.g[0][x];
-    const float omx = t.om[0][x];
-    const float fo = gxx * go * t.inv_p;
-    const float omo2 = gxx * go;
-    const float wx = col_weight(g, q, x);
+  };
+  auto prefetch_tile = [&](int b) {  // thread 0 only: DRAM -> L2 ahead of the load
+    int q, o, x0;
+    coords(b, q, o, x0);
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int p = l + LQ * j + M * r;  // group r holds frequencies k' + M r
-      const float omv = omx + gxx * omo + omo2 * __ldg(&omL[p]);  // 1 - g without cancellation
-      const float2 z = v[j];
-      acc += wx * omv * (z.x * z.x + z.y * z.y);
-      if (MODE == AXIS_FGI) {
-        const float f = fo * __ldg(&gL[p]);
-        v[j] = float2{z.x * f, z.y * f};
+    for (int bx = 0; bx < S::NBOX; ++bx) {
+      if (axis == 1) tma_prefetch_4d(&tm, x0, bx * S::BOX, o, q);
+      else tma_prefetch_4d(&tm, x0, o, bx * S::BOX, q);
+    }
+  };
+
+  if (tid == 0) {
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+    fence_barrier_init();
+    // the first tiles' loads go out before the tables are staged
+    for (int k = 0; k < NBUF && blockIdx.x + k * gridDim.x < ntiles; ++k)
+      issue_load(blockIdx.x + k * gridDim.x, k);
+    if (blockIdx.x + NBUF * gridDim.x < ntiles) prefetch_tile(blockIdx.x + NBUF * gridDim.x);
+    // the caller's L2 hint: this block's share of a buffer the next pass reads
+    if (pf_bytes > 0) {
+      const long long chunk = ((pf_bytes / gridDim.x + 4095) / 4096) * 4096;
+      const long long beg = chunk * blockIdx.x;
+      const long long end = beg + chunk < pf_bytes ? beg + chunk : pf_bytes;
+      for (long long o = beg; o < end; o += 65536) {
+        const long long n = end - o < 65536 ? end - o : 65536;
+        bulk_prefetch_l2(pf + o, (unsigned)(n & ~15LL));
       }
     }
   }
-  if (MODE == AXIS_FGI || MODE == AXIS_INV) F::inv(v, cbase, r, tw, twr, l);
-  if (MODE != AXIS_ENERGY) {
-    __syncthreads();  // every column's transposes are done: the tile is free
-#pragma unroll
-    for (int j = 0; j < E; ++j) tile[(R * (l + LQ * j) + r) * TS + c] = v[j];
-    __syncthreads();
-    for (int i = tid; i < L * TX; i += NT) {
-      const int p = i / TX, cc = i - p * TX;
-      base[(long long)p * es + cc] = tile[p * TS + cc];
+  {
+    const float2* tw = static_cast<const float2*>(t.tw[axis]);
+    for (int i = tid; i < L; i += NT) {
+      s_tw[i] = tw[i];
+      if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
+        s_g[i] = t.g[axis][i];
+        s_om[i] = t.om[axis][i];
+      }
     }
+  }
+  __syncthreads();
+
+  // the lane's rows are R (l + LQ j) + r; their swizzle term depends on l and r only
+  const int xr = ((((R * l + r) * TX * 8) >> 7) & S::SWM);
+  const int cs = c ^ (xr << 1);
+  const int lane_slot = (R * l + r) * TX + cs;
+  constexpr int JSTRIDE = R * LQ * TX;
+
+  float acc = 0.f;
+  bool ok = true;
+  int it = 0;
+  for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++it) {
+    const int buf = NBUF == 1 ? 0 : (it & 1);
+    const unsigned parity = NBUF == 1 ? (it & 1) : ((it >> 1) & 1);
+    float2* tile = reinterpret_cast<float2*>(al + buf * S::BUF_BYTES);
+    // this tile's per-column factors, loaded before the wait so that their
+    // latency overlaps it: g_x, 1 - g_x and the Parseval weight of column x
+    // (and g_y, 1 - g_y of the outer index in 3-D)
+    int q, o, x0;
+    coords(b, q, o, x0);
+    float gxx = 0.f, omx = 0.f, wx = 0.f, go = 1.f, omo = 0.f;
+    if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
+      const int x = x0 + c;
+      gxx = t.g[0][x];
+      omx = t.om[0][x];
+      wx = col_weight(g, q, x);
+      if (g.ndim == 3) {
+        go = t.g[1][o];
+        omo = t.om[1][o];
+      }
+    }
+    ok = __syncthreads_and(mbar_wait_bounded(&bar[buf], parity)) != 0;
+    if (!ok) break;
+    if (tid == 0 && it > 0 && b + NBUF * gridDim.x < ntiles) prefetch_tile(b + NBUF * gridDim.x);
+    float2 v[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = tile[lane_slot + j * JSTRIDE];
+    __syncthreads();  // the tile is in registers: its buffer holds the transposes now
+    float2* cbase = tile + c * PS;
+    const float2* tw = s_tw;
+    const float2* twr = s_tw + M;
+    if (MODE != AXIS_INV) F::fwd(v, cbase, r, tw, twr, l);
+    if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
+      // the last axis applies g(k) = g_x g_y (g_z); in 3-D the y frequency is
+      // the outer index o of this tile (the y pass ran before).
+      const float fo = gxx * go * t.inv_p;
+      const float omo2 = gxx * go;
+      const float omb = omx + gxx * omo;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int p = l + LQ * j + M * r;  // group r holds frequencies k' + M r
+        const float omv = omb + omo2 * s_om[p];  // 1 - g without cancellation
+        const float2 z = v[j];
+        acc += wx * omv * (z.x * z.x + z.y * z.y);
+        if (MODE == AXIS_FGI) {
+          const float f = fo * s_g[p];
+          v[j] = float2{z.x * f, z.y * f};
+        }
+      }
+    }
+    if (MODE == AXIS_FGI || MODE == AXIS_INV) F::inv(v, cbase, r, tw, twr, l);
+    __syncthreads();  // every column's transposes are done
+    const int nb = b + NBUF * gridDim.x;  // the tile that reuses this buffer
+    if (MODE != AXIS_ENERGY) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) tile[lane_slot + j * JSTRIDE] = v[j];
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+#pragma unroll
+        for (int bx = 0; bx < S::NBOX; ++bx) {
+          if (axis == 1) tma_store_4d(&tm, x0, bx * S::BOX, o, q, tile + bx * S::BOX * TX);
+          else tma_store_4d(&tm, x0, o, bx * S::BOX, q, tile + bx * S::BOX * TX);
+        }
+        bulk_commit();
+        if (nb < ntiles) {
+          bulk_wait_read_all();  // the store has read the buffer: the next load may overwrite it
+          issue_load(nb, buf);
+        }
+      }
+    } else if (tid == 0 && nb < ntiles) {
+      issue_load(nb, buf);
+    }
+  }
+  if (tid == 0) bulk_wait_all();
+  if (!ok) {
+    // a tile load did not land in time: record it, give the copies still in
+    // flight a bounded wait, and leave (statistics of this launch are void)
+    if (tid == 0) {
+      atomicOr(&sp.st->err, kErrWaitTimeout);
+      for (int k = 0; k < NBUF; ++k) (void)mbar_wait_bounded(&bar[k], 0), (void)mbar_wait_bounded(&bar[k], 1);
+    }
+    return;
   }
   if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
     const double tot = block_sum((double)acc, redd);
@@ -109,29 +234,60 @@ k_wcol(Geom g, Tables<float> t, float2* W, StatsPtrs sp, int axis) {
   }
 }
 
-template <int MODE, int L, int TX>
-cudaError_t wcol_m(const Geom& g, const Tables<float>& t, void* W, const StatsPtrs& sp, int axis,
-                   cudaStream_t s, bool prepare_only) {
-  auto k = k_wcol<MODE, L, TX>;
+// Blocks of a kernel that fit on one SM, and the SM count (cached per kernel).
+template <typename K> int persistent_blocks(K kernel, int threads, size_t smem, int& per_sm) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+template <int MODE, int L, int TX, int NBUF>
+cudaError_t wcol_m(const Geom& g, const Tables<float>& t, const CUtensorMap* tm, const StatsPtrs& sp,
+                   int axis, cudaStream_t s, bool prepare_only, const void* pf, long long pf_bytes) {
+  auto k = k_wcol<MODE, L, TX, NBUF>;
   static size_t done = 0;
-  const size_t smem = wcol_smem_bytes(L, TX);
+  static int slots = 0, per_sm = 0;
+  const size_t smem = wcol_smem<L, TX>(NBUF);
   cudaError_t e = set_smem_once(k, smem, done);
-  if (e != cudaSuccess || prepare_only) return e;
+  if (e != cudaSuccess) return e;
+  if (!slots) slots = persistent_blocks(k, WcolShape<L, TX>::NT, smem, per_sm);
+  if (prepare_only) return cudaSuccess;
+  if (!tm) return cudaErrorInvalidValue;
   const int nouter = axis == 1 ? g.nz : g.ny;
   const int tiles = col_tiles(g, nouter, TX);
-  k<<<tiles, TX * w_r(L) * w_lq(L), smem, s>>>(g, t, static_cast<float2*>(W), sp, axis);
+  const int blocks = tiles < slots ? tiles : slots;
+  k<<<blocks, WcolShape<L, TX>::NT, smem, s>>>(g, t, *tm, sp, axis, tiles,
+                                                static_cast<const char*>(pf), pf ? pf_bytes : 0);
   return cudaGetLastError();
 }
 
-template <int L, int TX>
-cudaError_t wcol_ltx(AxisMode mode, int axis, const Geom& g, const Tables<float>& t, void* W,
-                     const StatsPtrs& sp, cudaStream_t s, bool prep) {
+struct L2Hint {
+  const void* p;
+  long long bytes;
+};
+
+template <int L, int TX, int NB>
+cudaError_t wcol_ltxb(AxisMode mode, int axis, const Geom& g, const Tables<float>& t,
+                      const CUtensorMap* tm, const StatsPtrs& sp, cudaStream_t s, bool prep,
+                      L2Hint pf) {
   switch (mode) {
-    case AXIS_FWD: return wcol_m<AXIS_FWD, L, TX>(g, t, W, sp, axis, s, prep);
-    case AXIS_INV: return wcol_m<AXIS_INV, L, TX>(g, t, W, sp, axis, s, prep);
-    case AXIS_FGI: return wcol_m<AXIS_FGI, L, TX>(g, t, W, sp, axis, s, prep);
-    default: return wcol_m<AXIS_ENERGY, L, TX>(g, t, W, sp, axis, s, prep);
+    case AXIS_FWD: return wcol_m<AXIS_FWD, L, TX, NB>(g, t, tm, sp, axis, s, prep, pf.p, pf.bytes);
+    case AXIS_INV: return wcol_m<AXIS_INV, L, TX, NB>(g, t, tm, sp, axis, s, prep, pf.p, pf.bytes);
+    case AXIS_FGI: return wcol_m<AXIS_FGI, L, TX, NB>(g, t, tm, sp, axis, s, prep, pf.p, pf.bytes);
+    default: return wcol_m<AXIS_ENERGY, L, TX, NB>(g, t, tm, sp, axis, s, prep, pf.p, pf.bytes);
   }
+}
+
+template <int L, int TX>
+cudaError_t wcol_ltx(AxisMode mode, int axis, const Geom& g, const Tables<float>& t,
+                     const CUtensorMap* tm, const StatsPtrs& sp, cudaStream_t s, bool prep,
+                     int stages, L2Hint pf) {
+  if (stages == 2) return wcol_ltxb<L, TX, 2>(mode, axis, g, t, tm, sp, s, prep, pf);
+  return wcol_ltxb<L, TX, 1>(mode, axis, g, t, tm, sp, s, prep, pf);
 }
 
 }  // namespace
@@ -141,23 +297,70 @@ int warp_tile(int L, int nx, int tx) {
   return (nx % t == 0) ? t : 0;
 }
 
-size_t wcol_smem_bytes(int L, int tx) { return (size_t)L * (tx + 1) * sizeof(float2); }
+size_t wcol_smem_bytes(int L, int tx, int stages) {
+#define MBO_WSM(LEN)                                        \
+  if (L == LEN) return tx == 8 ? wcol_smem<LEN, 8>(stages) : wcol_smem<LEN, 4>(stages);
+  MBO_WSM(256)
+  MBO_WSM(512)
+  MBO_WSM(768)
+  MBO_WSM(1024)
+  MBO_WSM(1536)
+  MBO_WSM(2048)
+#undef MBO_WSM
+  return 0;
+}
+
+bool wcol_tensor_map(CUtensorMap* map, void* W, const Geom& g, int axis, int tx) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  const int L = axis == 1 ? g.ny : g.nz;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)g.Q};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.nx * g.ny * 8,
+                                 (cuuint64_t)g.P * 8};
+  const cuuint32_t bx = (cuuint32_t)(L < kBoxRows ? L : kBoxRows);
+  const cuuint32_t box[4] = {(cuuint32_t)tx, axis == 1 ? bx : 1u, axis == 1 ? 1u : bx, 1u};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = tx * 8 == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : tx * 8 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                               : CU_TENSOR_MAP_SWIZZLE_32B;
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t launch_wcol(AxisMode mode, int axis, const Geom& g, const Tables<float>& t, void* W,
-                        const StatsPtrs& sp, int tx, cudaStream_t s, bool prepare_only) {
+                        const StatsPtrs& sp, int tx, cudaStream_t s, bool prepare_only,
+                        const CUtensorMap* tm, int stages, const void* l2_hint,
+                        long long l2_hint_bytes) {
+  (void)W;  // addressed through the tensor map
+  const L2Hint pf{l2_hint, l2_hint_bytes};
   const int L = axis == 1 ? g.ny : g.nz;
   const int TX = warp_tile(L, g.nx, tx);
-#define MBO_WCOL_CASE(LEN)                                                          \
-  if (L == LEN) {                                                                   \
-    if (TX == 8) return wcol_ltx<LEN, 8>(mode, axis, g, t, W, sp, s, prepare_only); \
-    if (TX == 4) return wcol_ltx<LEN, 4>(mode, axis, g, t, W, sp, s, prepare_only); \
+#define MBO_WCOL_CASE(LEN)                                                              \
+  if (L == LEN) {                                                                       \
+    if (TX == 8) return wcol_ltx<LEN, 8>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf); \
+    if (TX == 4) return wcol_ltx<LEN, 4>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf); \
   }
   MBO_WCOL_CASE(1024)
   MBO_WCOL_CASE(512)
   MBO_WCOL_CASE(256)
   MBO_WCOL_CASE(768)
-  if (L == 1536 && TX == 4) return wcol_ltx<1536, 4>(mode, axis, g, t, W, sp, s, prepare_only);
-  if (L == 2048 && TX == 4) return wcol_ltx<2048, 4>(mode, axis, g, t, W, sp, s, prepare_only);
+  if (L == 1536 && TX == 4)
+    return wcol_ltx<1536, 4>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf);
+  if (L == 2048 && TX == 4)
+    return wcol_ltx<2048, 4>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf);
 #undef MBO_WCOL_CASE
   return cudaErrorInvalidValue;
 }

@@ -162,6 +162,10 @@ struct mbo_ctx {
   Tables<float> tf{};
   Tables<double> td{};
   int row_threads = 256, axis_threads = 256, tx = 8;
+  int axis_stages = 1;  // tile buffers per block of the FP32 warp-plan strided passes
+  // TMA descriptors of W for the FP32 warp-plan strided passes (index = axis)
+  CUtensorMap wmap[3];
+  bool wmap_ok[3] = {false, false, false};
   size_t bytes_total = 0;
   // workspace validity for MBO_STEP_CONTINUE
   const void* w_valid_for = nullptr;
@@ -310,7 +314,8 @@ StatsPtrs stats_ptrs(mbo_ctx* h, bool stats, bool respect_stop, double tol) {
 
 cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout,
                        const StatsPtrs& sp, cudaStream_t s);
-cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s);
+cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s,
+                        const void* l2_hint);
 
 cudaEvent_t take_event(mbo_ctx* h) {
   if (!h->ev_free.empty()) {
@@ -341,11 +346,12 @@ cudaError_t row_pass(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, cons
   return timed(h, pass, s, [&]() { return row_launch(h, mode, Ain, Aout, sp, s); });
 }
 
-cudaError_t axis_pass(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s) {
+cudaError_t axis_pass(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s,
+                      const void* l2_hint = nullptr) {
   const int pass = mode == AXIS_FWD ? MBO_PASS_AXIS_FWD
                    : mode == AXIS_INV ? MBO_PASS_AXIS_INV
                    : mode == AXIS_FGI ? MBO_PASS_AXIS_FGI : MBO_PASS_AXIS_ENERGY;
-  return timed(h, pass, s, [&]() { return axis_launch(h, mode, axis, sp, s); });
+  return timed(h, pass, s, [&]() { return axis_launch(h, mode, axis, sp, s, l2_hint); });
 }
 
 cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, const StatsPtrs& sp,
@@ -358,25 +364,38 @@ cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, co
                             static_cast<double*>(Aout), h->W, sp, 0.0, h->row_threads, s);
 }
 
-cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s) {
+// The field and the workspace together fit in L2 comfortably: the last
+// strided pass of a step may then pull the field (which the x pass reads for
+// its step statistics) into L2 while it transforms.
+constexpr size_t kL2HintBytes = 96u << 20;
+
+cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, cudaStream_t s,
+                        const void* l2_hint) {
+  const size_t abytes = (size_t)h->g.C * (size_t)h->g.P * h->elem;
+  const size_t wbytes = (size_t)h->g.Q * (size_t)h->g.P * 2 * h->elem;
+  if (abytes + wbytes > kL2HintBytes) l2_hint = nullptr;
   if (h->dtype == MBO_F32)
-    return launch_axis<float>(mode, axis, h->g, h->tf, h->W, sp, h->tx, h->axis_threads, s);
+    return launch_axis<float>(mode, axis, h->g, h->tf, h->W, sp, h->tx, h->axis_threads, s,
+                              h->wmap_ok[axis] ? &h->wmap[axis] : nullptr, h->axis_stages,
+                              l2_hint, l2_hint ? (long long)abytes : 0);
   return launch_axis<double>(mode, axis, h->g, h->td, h->W, sp, h->tx, h->axis_threads, s);
 }
 
 // Transform passes between the forward and the inverse x pass.
 // mode AXIS_FGI: diffuse; AXIS_ENERGY: energy only (workspace not restored in 3-D).
-cudaError_t middle_passes(mbo_ctx* h, AxisMode mode, const StatsPtrs& sp, cudaStream_t s) {
+// A_next: the field the following x pass reads (L2 hint), or nullptr.
+cudaError_t middle_passes(mbo_ctx* h, AxisMode mode, const StatsPtrs& sp, cudaStream_t s,
+                          const void* A_next = nullptr) {
   const StatsPtrs none = [&] {
     StatsPtrs n = sp;
     n.do_stats = 0;
     return n;
   }();
   cudaError_t e;
-  if (h->g.ndim == 2) return axis_pass(h, mode, 1, sp, s);
+  if (h->g.ndim == 2) return axis_pass(h, mode, 1, sp, s, A_next);
   if ((e = axis_pass(h, AXIS_FWD, 1, none, s)) != cudaSuccess) return e;
   if ((e = axis_pass(h, mode, 2, sp, s)) != cudaSuccess) return e;
-  if (mode == AXIS_FGI) return axis_pass(h, AXIS_INV, 1, none, s);
+  if (mode == AXIS_FGI) return axis_pass(h, AXIS_INV, 1, none, s, A_next);
   return cudaSuccess;
 }
 
@@ -428,6 +447,7 @@ void mbo_default_config(mbo_config* cfg) {
   cfg->row_threads = 0;
   cfg->axis_threads = 0;
   cfg->axis_tx = 0;
+  cfg->axis_stages = 0;
 }
 
 int64_t mbo_workspace_bytes(mbo_handle h) { return h ? (int64_t)h->bytes_total : 0; }
@@ -514,6 +534,13 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     }
     h->tx = c.axis_tx;
   }
+  if (c.axis_stages) {
+    if (c.axis_stages < 1 || c.axis_stages > 2) {
+      delete h;
+      return MBO_ERR_INVALID_ARG;
+    }
+    h->axis_stages = c.axis_stages;
+  }
   if (c.axis_threads) {
     if (c.axis_threads < 64 || c.axis_threads > kMaxThreads || c.axis_threads % 32) {
       delete h;
@@ -530,7 +557,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
       const int L = ax == 1 ? g.ny : g.nz;
       if (!axis_plan(g, ax, true).lq) continue;
       const int wt = warp_tile(L, g.nx, h->tx);
-      as = std::max(as, wcol_smem_bytes(L, wt));
+      as = std::max(as, wcol_smem_bytes(L, wt, h->axis_stages));
       min_tx = std::min(min_tx, wt);
     }
   }
@@ -581,11 +608,22 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     cudaMemcpy(h->tabs, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice);
     bind_tables(h, tb, h->td);
   }
-  const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx)
-                                          : prepare_kernels<double>(g, h->td, h->tx);
+  const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx, h->axis_stages)
+                                          : prepare_kernels<double>(g, h->td, h->tx, 1);
   if (pe != cudaSuccess) {
     mbo_destroy(h);
     return MBO_ERR_CUDA;
+  }
+  if (dtype == MBO_F32) {
+    for (int ax = 1; ax < ndim; ++ax) {
+      if (!h->tf.plan[ax].lq) continue;
+      const int L = ax == 1 ? g.ny : g.nz;
+      if (!wcol_tensor_map(&h->wmap[ax], h->W, g, ax, warp_tile(L, g.nx, h->tx))) {
+        mbo_destroy(h);
+        return MBO_ERR_CUDA;
+      }
+      h->wmap_ok[ax] = true;
+    }
   }
   if (cudaMemset(h->st, 0, sizeof(RunState)) != cudaSuccess ||
       cudaMemset(h->cnt, 0, (h->ngroups + 1) * sizeof(unsigned int)) != cudaSuccess ||
@@ -650,6 +688,17 @@ static mbo_status read_record(mbo_handle h, long long slot, mbo_stats* out) {
   return MBO_OK;
 }
 
+// Device error bits of the last synchronised read of the run state: a
+// kernel whose bounded wait gave up left them set.  The bits are cleared so
+// that later calls start clean.
+static mbo_status device_errors(mbo_handle h) {
+  const unsigned bits = h->h_st->err;
+  if (!bits) return MBO_OK;
+  h->h_st->err = 0;
+  cudaMemset(&h->st->err, 0, sizeof(unsigned int));
+  return fail(h, MBO_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (error bits 0x%x)", bits);
+}
+
 mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* stream) {
   if (!h) return MBO_ERR_INVALID_ARG;
   mbo_status rc;
@@ -663,6 +712,7 @@ mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* st
   if (stats) {
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+    if ((rc = device_errors(h)) != MBO_OK) return rc;
     const long long slot = (h->h_st->step - 1) & (kRing - 1);
     if ((rc = read_record(h, slot, stats)) != MBO_OK) return rc;
     if (stats->nonfinite) return fail(h, MBO_ERR_NUMERIC, "%lld non-finite points", (long long)stats->nonfinite);
@@ -682,6 +732,7 @@ mbo_status mbo_lyapunov(mbo_handle h, const void* A, double* E, void* stream) {
   h->w_valid_for = (h->g.ndim == 2) ? A : nullptr;
   CK(cudaStreamSynchronize(s));
   CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+  if ((rc = device_errors(h)) != MBO_OK) return rc;
   *E = h->h_st->energy_last;
   return MBO_OK;
 }
@@ -767,6 +818,7 @@ mbo_status mbo_run_until_stationary(mbo_handle h, void* A, int max_steps, double
     done += chunk;
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (mbo_status de = device_errors(h)) return de;
     stopped = h->h_st->stop != 0;
     mbo_status rc = harvest(h->h_st->step, false);
     if (rc != MBO_OK) return rc;

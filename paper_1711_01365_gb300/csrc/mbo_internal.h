@@ -1,6 +1,7 @@
 // Internal types shared by the host API (mbo_api.cu) and the kernels
 // (mbo_kernels.cuh).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,8 +62,12 @@ struct RunState {
   double energy_last;  // last energy written by a transform pass
   long long step;      // steps completed in this run
   int stop;            // 1 once a stationary step was seen (run loop only)
-  unsigned int pad_[3];
+  unsigned int err;    // device error bits (kErr*), surfaced by the host at sync points
+  unsigned int pad_[2];
 };
+
+// Device error bits of RunState::err.
+constexpr unsigned int kErrWaitTimeout = 1u;  // a bounded wait (copy or barrier) gave up
 
 // Step-record ring, indexed by step & (kRing - 1).
 struct Hist {
@@ -177,7 +182,9 @@ cudaError_t launch_row(RowMode mode, const Geom& g, const Tables<R>& t, const R*
                        cudaStream_t s);
 template <typename R>
 cudaError_t launch_axis(AxisMode mode, int axis, const Geom& g, const Tables<R>& t, void* W,
-                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s);
+                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s,
+                        const CUtensorMap* tm = nullptr, int stages = 1,
+                        const void* l2_hint = nullptr, long long l2_hint_bytes = 0);
 template <typename R>
 cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
                            double fallback_sigma, cudaStream_t s);
@@ -198,14 +205,20 @@ bool warp_plan_length(int N);
 int warp_plan_radix(int N);
 int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4 or 8; 0: none)
 size_t wrow_smem_bytes(const Geom& g, int N, bool fallback);
-size_t wcol_smem_bytes(int L, int tx);
+size_t wcol_smem_bytes(int L, int tx, int stages);
 cudaError_t launch_wrow(RowMode mode, const Geom& g, const Tables<float>& t, const float* A_in,
                         float* A_out, void* W, const StatsPtrs& sp, double fallback_sigma,
                         cudaStream_t s, bool prepare_only);
 cudaError_t launch_wcol(AxisMode mode, int axis, const Geom& g, const Tables<float>& t, void* W,
-                        const StatsPtrs& sp, int tx, cudaStream_t s, bool prepare_only);
+                        const StatsPtrs& sp, int tx, cudaStream_t s, bool prepare_only,
+                        const CUtensorMap* tm, int stages, const void* l2_hint = nullptr,
+                        long long l2_hint_bytes = 0);
+// TMA descriptor of the workspace W (4-D: x, y, z, plane; float2 elements)
+// with the box of the strided pass along `axis` (tile width tx).  Host.
+bool wcol_tensor_map(CUtensorMap* map, void* W, const Geom& g, int axis, int tx);
 
-template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& t, int tx);
+template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& t, int tx,
+                                                  int stages);
 template <typename R>
 cudaError_t launch_volume(int which, const Geom& g, const R* At, R* A, unsigned long long* keys,
                           SelectState* ss, const StatsPtrs& sp, double fb, int blocks,

@@ -644,9 +644,12 @@ static cudaError_t launch_axis_m(const Geom& g, const Tables<R>& t, void* W, con
 
 template <typename R>
 cudaError_t launch_axis(AxisMode mode, int axis, const Geom& g, const Tables<R>& t, void* W,
-                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s) {
+                        const StatsPtrs& sp, int tx, int threads, cudaStream_t s,
+                        const CUtensorMap* tm, int stages, const void* l2_hint,
+                        long long l2_hint_bytes) {
   if constexpr (sizeof(R) == 4) {
-    if (t.plan[axis].lq) return launch_wcol(mode, axis, g, t, W, sp, tx, s, false);
+    if (t.plan[axis].lq)
+      return launch_wcol(mode, axis, g, t, W, sp, tx, s, false, tm, stages, l2_hint, l2_hint_bytes);
   }
   switch (mode) {
     case AXIS_FWD: return launch_axis_m<R, AXIS_FWD>(g, t, W, sp, axis, tx, threads, s);
@@ -673,7 +676,8 @@ cudaError_t launch_project(const Geom& g, const R* At, R* B, int8_t* det_sign,
 // Raise the shared-memory limit of every kernel a geometry uses, without
 // launching (so that later launches inside stream capture make no attribute
 // call).
-template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& tabs, int tx) {
+template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>& tabs, int tx,
+                                                  int stages) {
   Tables<R> t{};
   StatsPtrs sp{};
   cudaError_t e = cudaSuccess;
@@ -685,7 +689,7 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>
     for (int axis = 1; axis <= (g.ndim == 3 ? 2 : 1) && e == cudaSuccess; ++axis) {
       if (!tabs.plan[axis].lq) continue;
       for (int m = AXIS_FWD; m <= AXIS_ENERGY && e == cudaSuccess; ++m)
-        e = launch_wcol((AxisMode)m, axis, g, tabs, nullptr, sp, tx, 0, true);
+        e = launch_wcol((AxisMode)m, axis, g, tabs, nullptr, sp, tx, 0, true, nullptr, stages);
     }
   }
 #define MBO_PREP_ROW(NM)                                                                       \
@@ -715,11 +719,12 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>
 }
 
 #define MBO_INSTANTIATE(R)                                                                     \
-  template cudaError_t prepare_kernels<R>(const Geom&, const Tables<R>&, int);                 \
+  template cudaError_t prepare_kernels<R>(const Geom&, const Tables<R>&, int, int);            \
   template cudaError_t launch_row<R>(RowMode, const Geom&, const Tables<R>&, const R*, R*,     \
                                      void*, const StatsPtrs&, double, int, cudaStream_t);      \
   template cudaError_t launch_axis<R>(AxisMode, int, const Geom&, const Tables<R>&, void*,     \
-                                      const StatsPtrs&, int, int, cudaStream_t);               \
+                                      const StatsPtrs&, int, int, cudaStream_t,                \
+                                      const CUtensorMap*, int, const void*, long long);        \
   template cudaError_t launch_project<R>(const Geom&, const R*, R*, int8_t*, double,          \
                                          cudaStream_t);                                        \
   template cudaError_t launch_volume<R>(int, const Geom&, const R*, R*, unsigned long long*,   \

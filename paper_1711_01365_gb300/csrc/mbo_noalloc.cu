@@ -102,8 +102,31 @@ mbo_status diffuse_noalloc(const Geom& g, const void* A, void* At, cudaStream_t 
     off = align256(off + (size_t)lens[ax] * sizeof(R));
   }
   if (off > (size_t)MBO_NOALLOC_SCRATCH_BYTES) return MBO_ERR_UNSUPPORTED_SIZE;
+  const int tx = pick_tx(g.nx, sizeof(R) == 4 ? 8 : 4);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MBO_ERR_CUDA;
+  // The row and strided passes keep whole rows / column tiles in shared
+  // memory: refuse, before any launch, a problem whose tiles exceed the
+  // device's per-block limit (as mbo_create does), so that no kernel
+  // attribute call can fail and leave an error behind.
+  int maxsm = 0;
+  if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return MBO_ERR_CUDA;
+  if (row_smem_bytes(g, sizeof(R), false) > (size_t)maxsm ||
+      axis_smem_bytes(std::max(g.ny, g.nz), tx, sizeof(R)) > (size_t)maxsm)
+    return MBO_ERR_UNSUPPORTED_SIZE;
+  // Both fields must live on the current device: the kernels and the scratch
+  // array used are those of the current device.
+  const void* fields[2] = {A, At};
+  for (const void* p : fields) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      (void)cudaGetLastError();  // the failed query's error is ours, not the caller's
+      return MBO_ERR_INVALID_ARG;
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return MBO_ERR_INVALID_ARG;
+    if (pa.device != dev) return MBO_ERR_INVALID_ARG;
+  }
   void* base = nullptr;
   if (scratch_address(dev, &base) != cudaSuccess) return MBO_ERR_CUDA;
   char* b = static_cast<char*>(base);
@@ -119,7 +142,6 @@ mbo_status diffuse_noalloc(const Geom& g, const void* A, void* At, cudaStream_t 
   }
   t.inv_p = (R)(1.0 / (double)g.P);
   void* W = base;
-  const int tx = pick_tx(g.nx, sizeof(R) == 4 ? 8 : 4);
   const int row_threads = g.nx >= 1024 ? 256 : (g.nx >= 256 ? 128 : (g.nx >= 64 ? 64 : 32));
   const int axis_threads = 256;
   StatsPtrs none{};

@@ -77,7 +77,16 @@ template <int DIR, int LEN, typename V> __device__ __forceinline__ void rdft(V* 
   else dft<DIR, LEN>(v);
 }
 
-template <int N, int LQ> struct WarpFFT {
+// Twiddle-table loads: TwGlobal reads a global table through the read-only
+// data path, TwShared a copy staged in shared memory.
+struct TwGlobal {
+  template <typename V> __device__ __forceinline__ static V ld(const V* p) { return __ldg(p); }
+};
+struct TwShared {
+  template <typename V> __device__ __forceinline__ static V ld(const V* p) { return *p; }
+};
+
+template <int N, int LQ, class TW = TwGlobal> struct WarpFFT {
   static constexpr int E = N / LQ;         // points per lane
   static constexpr int G = E / LQ;         // length-LQ DFTs per lane in the second step
   static constexpr int RS = (LQ + 1) * E;  // transpose region of one sequence (complex)
@@ -90,7 +99,7 @@ template <int N, int LQ> struct WarpFFT {
   __device__ __forceinline__ static void fwd(V (&v)[E], V* buf, const V* __restrict__ tw, int l) {
     rdft<-1, E>(v);
 #pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], __ldg(&tw[k2 * LQ + l]));
+    for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], TW::ld(&tw[k2 * LQ + l]));
 #pragma unroll
     for (int k2 = 0; k2 < E; ++k2) buf[k2 * (LQ + 1) + l] = v[k2];
     __syncwarp();
@@ -125,7 +134,7 @@ template <int N, int LQ> struct WarpFFT {
     __syncwarp();
 #pragma unroll
     for (int k2 = 1; k2 < E; ++k2) {
-      V c = __ldg(&tw[k2 * LQ + l]);
+      V c = TW::ld(&tw[k2 * LQ + l]);
       c.y = -c.y;
       v[k2] = cmul(v[k2], c);
     }
@@ -147,8 +156,8 @@ namespace mbo {
 // r-th of R consecutive regions of RS slots; for R > 1 the cross-group steps
 // end with a block barrier, so every thread of the block must call them.  For
 // R = 1 the calls are those of WarpFFT.
-template <int M, int LQ, int R> struct WarpFFTR {
-  using F = WarpFFT<M, LQ>;
+template <int M, int LQ, int R, class TW = TwGlobal> struct WarpFFTR {
+  using F = WarpFFT<M, LQ, TW>;
   static constexpr int E = F::E;
   static constexpr int RS = F::RS;
 
@@ -173,7 +182,7 @@ template <int M, int LQ, int R> struct WarpFFTR {
     F::fwd(v, base + r * RS, tw, l);
     if (r > 0) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&twr[(r - 1) * M + l + LQ * j]));
+      for (int j = 0; j < E; ++j) v[j] = cmul(v[j], TW::ld(&twr[(r - 1) * M + l + LQ * j]));
     }
 #pragma unroll
     for (int j = 0; j < E; ++j) base[r * RS + l + LQ * j] = v[j];
@@ -205,7 +214,7 @@ template <int M, int LQ, int R> struct WarpFFTR {
 #pragma unroll
       for (int s = 1; s < R; ++s) acc = cadd(acc, rot(base[s * RS + l + LQ * j], (R - 1) * s * r));
       if (r > 0) {
-        V c = __ldg(&twr[(r - 1) * M + l + LQ * j]);
+        V c = TW::ld(&twr[(r - 1) * M + l + LQ * j]);
         c.y = -c.y;
         acc = cmul(acc, c);
       }

@@ -57,7 +57,8 @@ class MboError(RuntimeError):
 
 class mbo_config(C.Structure):
     _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int),
-                ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int)]
+                ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int),
+                ("axis_stages", C.c_int)]
 
 
 class mbo_surface_params(C.Structure):
@@ -257,7 +258,25 @@ def mbo_run_until_stationary(h, A, max_steps: int, tol: float, stream=None) -> d
 
 def mbo_diffuse_noalloc(dims, n: int, tau: float, dtype: int, A, A_tilde, stream=None) -> None:
     """mbo_diffuse without a handle and without device allocation (scratch in a
-    static 64 MiB device array inside the library; see include/mbo.h)."""
+    static 64 MiB device array inside the library; see include/mbo.h).
+
+    With no handle to hold the sizes, tensor arguments are checked here: each
+    must be contiguous, hold n*n*prod(dims) values of the dtype's type and sit
+    on a CUDA device; ValueError otherwise (the kernels would read or write
+    past a smaller buffer)."""
+    want = int(n) * int(n) * int(np.prod([int(v) for v in dims]))
+    for name, t in (("A", A), ("A_tilde", A_tilde)):
+        if hasattr(t, "data_ptr") and hasattr(t, "numel"):
+            import torch
+            tdt = torch.float32 if int(dtype) == MBO_F32 else torch.float64
+            if t.numel() != want:
+                raise ValueError(f"{name} holds {t.numel()} values, the problem needs {want}")
+            if t.dtype != tdt:
+                raise ValueError(f"{name} is {t.dtype}, the call's dtype is {tdt}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} is not contiguous")
+            if not t.is_cuda:
+                raise ValueError(f"{name} is not on a CUDA device")
     d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
     _check(lib().mbo_diffuse_noalloc(len(dims), d, int(n), float(tau), int(dtype), _ptr(A),
                                      _ptr(A_tilde), _stream(stream)))
