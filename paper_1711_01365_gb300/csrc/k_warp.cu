@@ -191,7 +191,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     }
   }
   if (!sp.do_stats) return;
-  finalize_step_stats(sp, ps, redd, redi, &s_flag);
+  finalize_step_stats(g.P, g.tau, sp, ps, redd, redi, &s_flag);
 }
 
 template <int NM, int MODE, int N>

@@ -221,6 +221,13 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
   }
   if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
     const double tot = block_sum((double)acc, redd);
+    if (MODE == AXIS_FGI && sp.epart) {  // the x pass's finaliser adds these up
+      if (tid == 0) {
+        sp.epart[blockIdx.x] = tot;
+        if (blockIdx.x == 0) sp.st->nep = gridDim.x;
+      }
+      return;
+    }
     double all;
     if (grid_sum(tot, sp.rb, redd, &s_flag, &all)) {
       if (tid == 0) {

@@ -145,6 +145,7 @@ struct mbo_ctx {
   void* tabs = nullptr;  // twiddles, multipliers (one allocation)
   size_t tabs_bytes = 0;
   double* part = nullptr;     // per-block partials, then per-group totals
+  double* epart = nullptr;    // per-block energy partials of the fused step's multiplier pass
   unsigned int* cnt = nullptr;  // per-group arrival counters + the group counter
   size_t ngroups = 0;
   RunState* st = nullptr;
@@ -309,6 +310,7 @@ StatsPtrs stats_ptrs(mbo_ctx* h, bool stats, bool respect_stop, double tol) {
   sp.respect_stop = respect_stop ? 1 : 0;
   sp.do_stats = stats ? 1 : 0;
   sp.tol = tol;
+  sp.epart = nullptr;
   return sp;
 }
 
@@ -401,7 +403,8 @@ cudaError_t middle_passes(mbo_ctx* h, AxisMode mode, const StatsPtrs& sp, cudaSt
 
 // The steady-state step: middle passes + inverse x / projection / forward x.
 cudaError_t step_passes(mbo_ctx* h, void* A, bool respect_stop, double tol, cudaStream_t s) {
-  const StatsPtrs sp = stats_ptrs(h, true, respect_stop, tol);
+  StatsPtrs sp = stats_ptrs(h, true, respect_stop, tol);
+  sp.epart = h->epart;  // the energy is reduced by the x pass's finaliser
   cudaError_t e = middle_passes(h, AXIS_FGI, sp, s);
   if (e != cudaSuccess) return e;
   return row_pass(h, ROW_INV_PROJECT_FWD, nullptr, A, sp, s);
@@ -468,6 +471,7 @@ mbo_status mbo_destroy(mbo_handle h) {
   cudaFree(h->part);
   cudaFree(h->cnt);
   cudaFree(h->st);
+  cudaFree(h->epart);
   cudaFree(h->hist_mem);
   cudaFree(h->field);
   cudaFree(h->vp_at);
@@ -583,6 +587,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   h->ngroups = (nparts + kReduceGroup - 1) / kReduceGroup;
   if (!alloc(&h->W, wbytes) ||
       !alloc((void**)&h->part, (h->ngroups * kReduceGroup + h->ngroups) * sizeof(double)) ||
+      !alloc((void**)&h->epart, h->ngroups * kReduceGroup * sizeof(double)) ||
       !alloc((void**)&h->cnt, (h->ngroups + 1) * sizeof(unsigned int)) ||
       !alloc((void**)&h->st, sizeof(RunState)) ||
       !alloc(&h->hist_mem, (size_t)kRing * 5 * sizeof(double))) {

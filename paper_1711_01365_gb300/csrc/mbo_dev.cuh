@@ -668,6 +668,76 @@ __device__ __forceinline__ R polar_newton(const R* m, R* b, R& est, R skip_below
   return det >= R(0) ? R(1) : R(-1);
 }
 
+// n = 3, FP32: a fixed schedule of the same iteration -- two Frobenius-
+// scaled steps, then two unscaled ones -- with no convergence test inside.
+// Newton's iteration for the polar factor converges quadratically, so when
+// the last unscaled step moved no entry by more than kPolarAccept the
+// remaining error is below about kPolarAccept^2 / 2 (5e-8, under the FP32
+// rounding of the iterate itself) and b is accepted;
+// else `done` is false and b holds the current iterate for the caller to
+// finish.  est and the routing of small or singular points are as in
+// polar_newton (points not iterated at all return done = true with est <=
+// skip_below).  The returned class is the sign of det of the last iterate.
+constexpr float kPolarAccept = 3e-4f;
+
+__device__ __forceinline__ float polar3_fixed(const float* m, float* b, float& est, float skip_below,
+                                              float cof2_floor, bool& done) {
+  float X[9], C[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X[k] = m[k];
+  float det = cofactor3(X, C);
+  const float sg = (det >= 0.f) ? 1.f : -1.f;
+  float nx = 0.f, nc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    nx += X[k] * X[k];
+    nc += C[k] * C[k];
+  }
+  est = fabsf(det) * rsqrtf(nc);
+  if (!(nc > cof2_floor)) est = 0.f;
+  done = true;
+  if (!(est > skip_below)) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b[k] = X[k];
+    return sg;
+  }
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // scaled: zeta = (|X^-1|_F / |X|_F)^(1/2)
+    if (it > 0) {
+      det = cofactor3(X, C);
+      nx = 0.f;
+      nc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        nx += X[k] * X[k];
+        nc += C[k] * C[k];
+      }
+    }
+    const float zf = rsqrtf(rsqrtf(__fdividef(nc, det * det * nx)));
+    const float a = 0.5f * zf;
+    const float c = __fdividef(0.5f, zf * det);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = a * X[k] + c * C[k];
+  }
+  float delta = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // unscaled
+    det = cofactor3(X, C);
+    const float c = 0.5f * __frcp_rn(det);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xn = 0.5f * X[k] + c * C[k];
+      if (it == 1) delta = fmaxf(delta, fabsf(xn - X[k]));
+      X[k] = xn;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) b[k] = X[k];
+  done = delta <= kPolarAccept;  // NaN: not done
+  if (!(fabsf(X[0]) < 1e30f)) est = 0.f;
+  return det >= 0.f ? 1.f : -1.f;
+}
+
 template <int ITMAX, int NUN, typename R>
 __device__ __forceinline__ R polar3_newton(const R* m, R* b, R& est, R skip_below = R(0),
                                            R cof2_floor = R(0)) {
@@ -1012,8 +1082,9 @@ __device__ __forceinline__ double sum_partials(const double* p, int count, doubl
   return block_sum(acc, red);
 }
 
-// Deterministic grid-wide sum of one double per block (thread 0's v), in two
-// levels: blocks are grouped by kReduceGroup consecutive indices; the last
+// Deterministic grid-wide sum of one double per block (thread 0's v).  Up to
+// kReduceOneLevel blocks, the last block to arrive sums all partials in index
+// order (one round of fence and counter); larger grids take two levels: blocks are grouped by kReduceGroup consecutive indices; the last
 // block of a group to finish sums that group's partials in index order, and
 // the last group to finish sums the group totals in index order.  Returns
 // true in exactly one block, whose thread 0 receives the total.  The
@@ -1021,6 +1092,17 @@ __device__ __forceinline__ double sum_partials(const double* p, int count, doubl
 __device__ __forceinline__ bool grid_sum(double v, const ReduceBufs& rb, double* red, int* s_flag,
                                          double* total) {
   const unsigned nb = gridDim.x, b = blockIdx.x;
+  if (nb <= kReduceOneLevel) {
+    // one level: the last block to arrive sums every partial in index order
+    if (threadIdx.x == 0) rb.part[b] = v;
+    if (!last_to_arrive(&rb.gcount[0], nb, s_flag)) return false;
+    const double t = sum_partials(rb.part, (int)nb, red);
+    if (threadIdx.x == 0) {
+      *total = t;
+      rb.gcount[0] = 0;
+    }
+    return true;
+  }
   const unsigned grp = b / kReduceGroup;
   const unsigned ngroups = (nb + kReduceGroup - 1) / kReduceGroup;
   const unsigned gsize = min((unsigned)kReduceGroup, nb - grp * kReduceGroup);

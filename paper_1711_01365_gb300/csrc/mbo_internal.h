@@ -63,7 +63,8 @@ struct RunState {
   long long step;      // steps completed in this run
   int stop;            // 1 once a stationary step was seen (run loop only)
   unsigned int err;    // device error bits (kErr*), surfaced by the host at sync points
-  unsigned int pad_[2];
+  unsigned int nep;    // blocks of the last transform pass that left energy partials in epart
+  unsigned int pad_;
 };
 
 // Device error bits of RunState::err.
@@ -143,6 +144,7 @@ enum RowMode { ROW_FWD = 0, ROW_INV_OUT = 1, ROW_INV_PROJECT_FWD = 2 };
 
 // Buffers of the deterministic two-level grid sum (see grid_sum).
 constexpr int kReduceGroup = 256;
+constexpr unsigned kReduceOneLevel = 2048;  // grids up to this size reduce in one level
 struct ReduceBufs {
   double* part;          // one partial per block
   double* gpart;         // one total per group of kReduceGroup blocks
@@ -157,6 +159,13 @@ struct StatsPtrs {
   int respect_stop;    // 1: return at once if st->stop is set
   int do_stats;        // 1: accumulate and finalise statistics
   double tol;          // stationarity tolerance (< 0: never stop)
+  // Deferred energy (fused step only; nullptr otherwise): the multiplier pass
+  // leaves one Parseval partial per block here (and the block count in
+  // RunState::nep) instead of reducing them itself, and the x pass's
+  // finaliser, which runs next and reduces anyway, adds them up in block
+  // order and records E^tau.  This takes one grid-wide reduction off the
+  // critical path of each step.
+  double* epart;
 };
 
 // Radix selection of the n_plus smallest (key, index) pairs (volume-preserving

@@ -43,6 +43,16 @@ template <int NM> struct ProjV {
   float gap;
 };
 
+// Points the fixed FP32 n = 3 schedule did not settle: the convergence-tested
+// iteration, continued from the current iterate.
+static __device__ __noinline__ ProjV<3> newton_cold(MatV<3> x) {
+  ProjV<3> r;
+  float est = 0.f;
+  r.sg = polar_newton<3, 10, 2>(x.v, r.b, est, 0.f, 0.f);
+  r.gap = est;
+  return r;
+}
+
 template <int NM> __device__ __noinline__ ProjV<NM> quat_cold(MatV<NM> m, float sg) {
   ProjV<NM> r;
   r.sg = sg;
@@ -90,7 +100,22 @@ __device__ __forceinline__ bool project_point(const R* m, R* b, R& sg, R fb) {
     const float lim = fmaxf(fb, 1e-6f * sqrtf(nx));
     // |cof m|_F > 1e-5 |m|_F^(n-1): above the FP32 rounding error of cof
     const float cf = NM == 3 ? nx * nx : nx * nx * nx;
-    sg = polar_newton<NM, 10, 2>(m, b, est, lim, 1e-10f * cf);
+    if constexpr (NM == 3) {
+      bool done;
+      sg = polar3_fixed(m, b, est, lim, 1e-10f * cf, done);
+      if (est > lim && !done) {
+        MatV<3> xv;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) xv.v[k] = b[k];
+        const ProjV<3> r = newton_cold(xv);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b[k] = r.b[k];
+        sg = r.sg;
+        if (!(fabsf(b[0]) < 1e30f)) est = 0.f;
+      }
+    } else {
+      sg = polar_newton<NM, 10, 2>(m, b, est, lim, 1e-10f * cf);
+    }
     if (est > lim) return true;
     if constexpr (NM == 3) {
       MatV<3> mv;
@@ -155,8 +180,9 @@ __device__ __forceinline__ void finish_point(R* __restrict__ A, long long P, lon
 // delta, flips, re-projections, non-finite count), decide stationarity
 // (tol >= 0), reset the accumulators and advance the step counter.
 template <typename R>
-__device__ __forceinline__ void finalize_step_stats(const StatsPtrs& sp, const PointStats<R>& ps,
-                                                    double* redd, int* redi, int* s_flag) {
+__device__ __forceinline__ void finalize_step_stats(long long P, double tau, const StatsPtrs& sp,
+                                                    const PointStats<R>& ps, double* redd, int* redi,
+                                                    int* s_flag) {
   const int tid = threadIdx.x;
   const double dsum = block_sum((double)ps.defect, redd);
   const double mx = block_max((double)ps.maxd, redd);
@@ -171,10 +197,19 @@ __device__ __forceinline__ void finalize_step_stats(const StatsPtrs& sp, const P
   }
   double all;
   if (grid_sum(dsum, sp.rb, redd, s_flag, &all)) {
+    // deferred energy of this step's input: the multiplier pass's partials
+    // (block order) with the defect of A_s, still in st->defect
+    const double esum = sp.epart ? sum_partials(sp.epart, (int)sp.st->nep, redd) : 0.0;
     if (tid == 0) {
       RunState* st = sp.st;
-      st->defect = all;
       const long long slot = st->step & (kRing - 1);
+      if (sp.epart) {
+        const double Pd = (double)P;
+        const double E_tau = (esum / Pd + st->defect) / (Pd * tau);
+        st->energy_last = E_tau;
+        sp.hist.energy[slot] = E_tau;
+      }
+      st->defect = all;
       const double md = __longlong_as_double((long long)atomicAdd(&st->maxdelta_bits, 0ull));
       const unsigned long long f = atomicAdd(&st->flips, 0ull);
       const unsigned long long nb = atomicAdd(&st->fallback, 0ull);
@@ -320,7 +355,7 @@ k_row(Geom g, Tables<R> t, const R* __restrict__ Ain, R* A, typename VT<R>::V* W
     for (int x = tid; x < nx; x += T) W[q * P + off + x] = s[lay.addr(q, x)];
 
   if (!sp.do_stats) return;
-  finalize_step_stats(sp, ps, redd, redi, &s_flag);
+  finalize_step_stats(g.P, g.tau, sp, ps, redd, redi, &s_flag);
 }
 
 // Strided-axis pass (y in 2-D; y and z in 3-D).  One block owns a tile of tx
@@ -395,6 +430,13 @@ k_axis(Geom g, Tables<R> t, typename VT<R>::V* W, StatsPtrs sp, int axis, int lt
   }
   if ((MODE == AXIS_FGI || MODE == AXIS_ENERGY) && sp.do_stats) {
     const double tot = block_sum((double)acc, redd);
+    if (MODE == AXIS_FGI && sp.epart) {  // the x pass's finaliser adds these up
+      if (tid == 0) {
+        sp.epart[blockIdx.x] = tot;
+        if (blockIdx.x == 0) sp.st->nep = gridDim.x;
+      }
+      return;
+    }
     double all;
     if (grid_sum(tot, sp.rb, redd, &s_flag, &all)) {
       if (tid == 0) {
@@ -550,7 +592,7 @@ k_vp_assign(long long P, const R* __restrict__ At, R* A, const unsigned long lon
     ps.flips += ((od > R(0)) != sel) ? 1 : 0;
   }
   if (!sp.do_stats) return;
-  finalize_step_stats(sp, ps, redd, redi, &s_flag);
+  finalize_step_stats(P, 0.0, sp, ps, redd, redi, &s_flag);  // the energy is the FGI pass's (no epart)
 }
 
 template <typename R>
