@@ -12,6 +12,15 @@ on the launching stream with a 256 MB L2-flushing read between steps (outside
 the events); barrier + synchronize on both sides; max over ranks.  The field
 and its workspace (~80 MB) would otherwise stay in the 129 MB L2.
 
+Sub-lines of the same JSON line: the FP64 form (with its ALU roofline against
+the measured DFMA rate), the FP32 form with FP64 re-projection below
+sigma_min = 1e-3, the 96-field batch, the 128^2 n=2 FP64 run (c1), the 256^3
+and 512^3 fields (c3, c5), the measured SIMT multiply-add peaks, and an
+accuracy block: one step of each form against one oracle step from the same
+input, and 200-step runs against the stored oracle run.  The roofline uses
+the minimal 2-D schedule's algorithmic bytes: 2S per fused pass, 4S per step
+(S = P n^2 w).
+
 Multi-GPU: the path has no exchange step; each rank iterates its own field
 (replicas, weak scaling, no collective on the data path).
 
@@ -264,7 +273,7 @@ def bench_batched(args, torch, M):
     b.step(A)
     for _ in range(max(args.warmup - 1, 0)):
         b.step(A, flags=M.MBO_STEP_CONTINUE)
-    K = max(3, min(args.steps, 10))
+    K = max(3, args.steps)
     s = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
@@ -281,6 +290,158 @@ def bench_batched(args, torch, M):
             "ms_per_step": 1e3 * t / K, "dtype": "f32",
             "note": "96 fields 256^2..2048^2, n=2/3, tau=4h^2, one graph launch per batch step, "
                     "working set > L2 (no flush)"}
+
+
+EPS32 = 2.0 ** -24
+
+
+def accuracy_block(torch, M, A_in32, n, tau):
+    """One step of each form from the same input (the FP32 field after the
+    timed steps, taken exactly in FP64) against one FP64 oracle step:
+    max-entry error (all points; points whose |det A~| is above the FP32
+    rounding level 64 eps |A~|_F^n; of those, points with sigma_2 + sigma_3 >=
+    1e-2), orthogonality defect max |B^t B - I|, energy relative error and
+    det-flip counts.  Host time: one oracle step plus an SVD per point."""
+    from oracle import oracle as O
+
+    dims = tuple(A_in32.shape[1:])
+    A_in = A_in32.double().cpu().numpy()
+    O.set_threads(0)
+    ref, st = O.step(A_in, n, tau)
+    At = O.diffuse(A_in, tau)
+    mats = np.moveaxis(At.reshape(n * n, -1), 0, -1).reshape(-1, n, n)
+    sv = np.linalg.svd(mats, compute_uv=False)
+    cs = sv[:, -1] + sv[:, -2]
+    absdet = np.prod(sv, axis=1)
+    cut = 64 * EPS32 * np.sqrt((sv ** 2).sum(axis=1)) ** n
+    out = {"input": "the FP32 field after the timed steps, exactly in FP64; one step of each form vs one FP64 oracle step",
+           "oracle_energy": st["energy"], "oracle_det_flips": int(st["det_flips"])}
+    for form, tdt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        h = M.Mbo(dims, n, tau, form.replace("fp", "f"))
+        t = torch.tensor(A_in, dtype=tdt, device="cuda")
+        rec = h.step(t, want_stats=True)
+        B = t.double().cpu().numpy()
+        h.close()
+        err = np.abs(B - ref).reshape(n * n, -1).max(axis=0)
+        Bm = np.moveaxis(B.reshape(n * n, -1), 0, -1).reshape(-1, n, n)
+        orth = np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max()
+        unamb = absdet > (cut if form == "fp32" else 1e-12)
+        well = unamb & (cs >= 1e-2)
+        out[form] = {"max_entry_err_all": float(err.max()),
+                     "max_entry_err_unambiguous": float(err[unamb].max()),
+                     "max_entry_err_sigma23_ge_1e-2": float(err[well].max()),
+                     "points_det_at_rounding_level": int((~unamb).sum()),
+                     "orthogonality_defect": float(orth),
+                     "energy_rel_err": abs(rec["energy"] - st["energy"]) / abs(st["energy"]),
+                     "det_flips": int(rec["det_flips"])}
+    return out
+
+
+def trajectory_block(torch, M):
+    """200 steps of the 1024^2 n=3 workload from the oracle's projection of
+    the raw field, both forms, against the FP64 oracle run stored in
+    tests/golden/c2_trajectory_fp64.txt: stationary step counts, the number of
+    leading steps whose det-sign flip counts agree, and the largest energy
+    relative error over those steps."""
+    from oracle import oracle as O
+
+    path = os.path.join(ROOT, "tests", "golden", "c2_trajectory_fp64.txt")
+    if not os.path.exists(path):
+        return None
+    g_steps, g_stat, rows = None, None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# steps="):
+                kv = dict(x.split("=") for x in line[2:].split()[:2])
+                g_steps, g_stat = int(kv["steps"]), bool(int(kv["stationary"]))
+            elif not line.startswith("#"):
+                rows.append(line.split())
+    g_en = np.array([float(r[1]) for r in rows])
+    g_fl = np.array([int(r[3]) for r in rows[:-1]])
+    F, n, tau = I.config_field(WORKLOAD)
+    A0 = O.project(F, n)
+    out = {"oracle_steps": g_steps, "oracle_stationary": g_stat, "max_steps": 200, "tol": 1e-4}
+    for form, tdt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        h = M.Mbo(F.shape[1:], n, tau, form.replace("fp", "f"))
+        t = torch.tensor(A0, dtype=tdt, device="cuda")
+        r = h.run(t, 200, 1e-4)
+        h.close()
+        fl = np.asarray(r["det_flips"])
+        k = min(len(fl), len(g_fl))
+        diff = np.nonzero(fl[:k] != g_fl[:k])[0]
+        agree = int(diff[0]) if len(diff) else k
+        en = np.asarray(r["energies"])
+        m = min(len(en), len(g_en), agree + 1)
+        out[form] = {"steps": int(r["steps"]), "stationary": bool(r["stationary"]),
+                     "steps_flips_agree": agree,
+                     "max_energy_rel_err_while_agreeing": float(np.max(np.abs(en[:m] - g_en[:m]) / np.abs(g_en[:m])))}
+    return out
+
+
+def bench_c1(torch, M, steps):
+    """128^2, n=2, FP64, tau=4h^2: graph-replayed run of `steps` steps (never
+    stopping) from the projected Gaussian field; launch-latency bound."""
+    from oracle import oracle as O
+
+    F, n, tau = I.config_field("C1")
+    A0 = O.project(F, n)
+    h = M.Mbo(F.shape[1:], n, tau, "f64")
+    t = torch.tensor(A0, dtype=torch.float64, device="cuda")
+    h.run(t, 10, -1.0)  # warm-up (captures the step graph)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    r = h.run(t, steps, -1.0)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h.close()
+    P = int(np.prod(F.shape[1:]))
+    return {"workload": "2-D flat torus 128x128, n=2 (O_2), tau=4h^2, FP64, graph-replayed run",
+            "value": P * r["steps"] / (ms / 1e3), "unit": UNIT, "steps": int(r["steps"]),
+            "us_per_step": 1e3 * ms / r["steps"], "dtype": "f64",
+            "note": "mbo_run_until_stationary with tol < 0 (no early stop); includes the run's "
+                    "host polls of the step records; the field fits in L2 (launch-latency bound)"}
+
+
+def bench_3d(torch, M, name, steps, warmup, hbm, peak_kind):
+    """K steady-state steps of a 3-D workload (FP32, n=3), each between CUDA
+    events without per-pass events; then a profiled set of steps for the pass
+    times.  The fields exceed L2, so no flush is needed."""
+    F, n, tau = I.config_field(name, dtype=np.float32)
+    dims = tuple(F.shape[1:])
+    P = int(np.prod(dims))
+    h = M.Mbo(dims, n, tau, "f32")
+    raw = torch.from_numpy(F).cuda()
+    del F
+    A = torch.empty_like(raw)
+    h.project(raw, A)
+    del raw
+    h.step(A)
+    for _ in range(max(warmup - 1, 0)):
+        h.step(A, flags=M.MBO_STEP_CONTINUE)
+    torch.cuda.synchronize()
+    ms, _ = time_steps(torch, h, A, steps, lambda: None, prof=False)
+    _, passes = time_steps(torch, h, A, 2, lambda: None, prof=True)
+    h.close()
+    del A
+    torch.cuda.empty_cache()
+    t = sum(ms) / 1e3 / steps
+    C, Q, nx = n * n, (n * n + 1) // 2, dims[-1]
+    xh = min(nx, ((nx // 2 + 1 + 15) // 16) * 16) if (C % 2 and nx in (256, 512, 1024)) else nx
+    w_bytes = ((Q - 1) * nx + xh) * (P // nx) * 2 * 4
+    S = C * P * 4
+    pt = {k: v[0] / 1e3 / max(v[1], 1) for k, v in passes.items() if v[1]}
+    # SURVEY 8(d): a 3-D step moves 8S algorithmic bytes (four passes, each reading and writing the field's bytes)
+    return {"workload": f"3-D flat torus {'x'.join(map(str, dims))}, n=3, FP32, tau=2h^2",
+            "value": P / t, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * t, "dtype": "f32",
+            "roofline": {"bound": "hbm", "achieved": 8 * S / t / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": 8 * S / t / 1e9 / hbm, "peak_kind": peak_kind,
+                         "alg_bytes_per_step": 8 * S, "basis": "8S per step (four passes over the field bytes S)",
+                         "passes_us": {k: v * 1e6 for k, v in pt.items()},
+                         "step_bytes_as_built": 2 * w_bytes * 3 + 2 * w_bytes + 2 * S},
+            "l2": "field larger than L2 (no flush)"}
 
 
 def run_ours(args, ws, rank, local):
@@ -347,20 +508,25 @@ def run_ours(args, ws, rank, local):
     a_bytes = C * P * elem
     row_ms, row_n = passes["row_project"]
     ax_ms, ax_n = passes["axis_fgi"]
-    row_alg = 2 * w_bytes + 2 * a_bytes  # read W, read old A, write A, write W
-    ax_alg = 2 * w_bytes                 # read W, write W
+    # algorithmic bytes of the minimal 2-D schedule (two fused passes, each
+    # reading and writing the field's bytes S = P n^2 w): 2S per pass, 4S per step
+    S = a_bytes
     row_t = row_ms / 1e3 / max(row_n, 1)
     ax_t = ax_ms / 1e3 / max(ax_n, 1)
-    dominant = ("row_project", row_alg, row_t) if row_ms >= ax_ms else ("axis_fgi", ax_alg, ax_t)
-    achieved = dominant[1] / dominant[2] / 1e9
+    dominant = ("row_project", row_t) if row_ms >= ax_ms else ("axis_fgi", ax_t)
+    achieved = 2 * S / dominant[1] / 1e9
     traffic = recorded_traffic("k_wrow" if dominant[0] == "row_project" else "k_wcol")
     roofline = {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic,
-                "alg_bytes_per_launch": dominant[1], "launch_us": dominant[2] * 1e6,
+                "alg_bytes_per_launch": 2 * S, "launch_us": dominant[1] * 1e6,
+                "basis": "2S per fused pass, 4S per step (S = P n^2 w, the field's bytes)",
                 "passes_us": {"row_project": row_t * 1e6, "axis_fgi": ax_t * 1e6},
-                "step_alg_bytes": row_alg + ax_alg,
-                "step_frac": (row_alg + ax_alg) / (t32 / args.steps) / 1e9 / hbm}
+                "step_alg_bytes": 4 * S,
+                "step_frac": 4 * S / (t32 / args.steps) / 1e9 / hbm,
+                "as_built_bytes": {"row_project": 2 * w_bytes + 2 * a_bytes, "axis_fgi": 2 * w_bytes,
+                                   "note": "x pass: read W, read the old field for the step "
+                                           "statistics, write the field, write W; y pass: read W, write W"}}
 
     # ---- FP64 form (plain), same workload ----
     fp64 = None
@@ -379,11 +545,53 @@ def run_ours(args, ws, rank, local):
                 "ms_per_step": 1e3 * t64 / K64,
                 "passes_us": {k: 1e3 * v[0] / max(v[1], 1) for k, v in p64.items() if v[1]}}
 
+    # ---- FP32 form with the FP64 re-projection trigger at sigma_min < 1e-3 ----
+    fb3 = None
+    if not args.no_fp64:
+        hf = M.Mbo(dims, n, tau, "f32", fallback_sigma=1e-3)
+        Af = A0.float().contiguous()
+        hf.step(Af)
+        for _ in range(max(args.warmup - 1, 0)):
+            flush()
+            hf.step(Af, flags=M.MBO_STEP_CONTINUE)
+        barrier()
+        msf, _ = time_steps(torch, hf, Af, args.steps, flush, prof=False)
+        barrier()
+        recf = hf.step(Af, flags=M.MBO_STEP_CONTINUE, want_stats=True)
+        vf, tf = job_throughput(P, args.steps, sum(msf) / 1e3, device="cuda")
+        fb3 = {"value": vf, "unit": UNIT, "ms_per_step": 1e3 * tf / args.steps,
+               "fallback_points_per_step": int(recf["fallback_points"]),
+               "note": "fallback_sigma = 1e-3: n=3 points whose smallest-singular-value estimate "
+                       "is below 1e-3 are re-projected in FP64 (the headline uses the default 0: "
+                       "quaternion form, FP64 only where (sigma_2+sigma_3)/|A| is small too)"}
+        hf.close()
+        del Af
+
     # ---- batched form: 96 independent uneven fields (256^2 .. 2048^2, n = 2, 3) ----
     batched = None
     if not args.no_batch:
         batched = bench_batched(args, torch, M)
+
+    # ---- the other configurations: 128^2 n=2 FP64 (launch-latency bound), 256^3 and 512^3 ----
+    c1 = c3 = c5 = None
+    if not args.no_extra:
+        c1 = bench_c1(torch, M, 100)
+        c3 = bench_3d(torch, M, "C3", 5, 3, hbm, peak_kind)
+        c5 = bench_3d(torch, M, "C5", 3, 3, hbm, peak_kind)
+    # ---- measured SIMT pipe peaks; the FP64 form's ALU roofline ----
+    peaks = M.mbo_measure_fma_peaks()
     clocks = clk.stop()
+    if fp64 is not None:
+        # algorithmic FP64 flops per point and step: four length-1024 complex
+        # transforms of the 5 planes (5 N log2 N each: 50 per element), the
+        # multiplier (2 per element) and the scaled Newton polar factor of a
+        # 3x3 (about 95 flops per scaled and 59 per unscaled iteration; about
+        # four scaled and three unscaled)
+        flops_pt = 5 * (4 * 50 + 2) + (4 * 95 + 3 * 59)
+        ach = flops_pt * P / (fp64["ms_per_step"] / 1e3) / 1e12
+        fp64["roofline"] = {"bound": "fp64_alu", "achieved": ach, "peak": peaks["fp64"], "unit": "TFLOP/s",
+                            "frac": ach / peaks["fp64"], "peak_kind": "measured (mbo_measure_fma_peaks, DFMA)",
+                            "alg_flops_per_point_step": flops_pt}
 
     # ---- run loop as a user runs it (graph replay, L2 left warm) ----
     Arun = A0.float().contiguous()
@@ -411,6 +619,11 @@ def run_ours(args, ws, rank, local):
            "steps_per_call": args.run_steps,
            "note": "mbo_run_until_stationary on a pinned host field: H2D, all iterations, D2H"}
 
+    accuracy = None
+    if rank == 0 and not args.no_accuracy:
+        accuracy = accuracy_block(torch, M, A32, n, tau)
+        accuracy["trajectory"] = trajectory_block(torch, M)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
@@ -436,8 +649,12 @@ def run_ours(args, ws, rank, local):
             "e2e": e2e,
             "gpu_launches": sum(v[1] for v in passes.values()),
             "clocks": clocks,
+            "accuracy": accuracy,
             "fp64": fp64,
+            "fp32_fallback_sigma_1e-3": fb3,
             "batched": batched,
+            "c1": c1, "c3": c3, "c5": c5,
+            "simt_peaks_tflops": peaks,
             "run_loop": run_loop,
         }
         print(json.dumps(line), flush=True)
@@ -484,8 +701,9 @@ def run_3d(args, ws, rank, local):
     for _ in range(max(args.warmup - 1, 0)):
         h.step(A, flags=M.MBO_STEP_CONTINUE)
     barrier()
-    ms, passes = time_steps(torch, h, A, args.steps, lambda: None)
+    ms, _ = time_steps(torch, h, A, args.steps, lambda: None, prof=False)
     barrier()
+    _, passes = time_steps(torch, h, A, 2, lambda: None, prof=True)
     clocks = clk.stop()
     value, t = job_throughput(P, args.steps, sum(ms) / 1e3, device="cuda")
     hbm, peak_kind = load_peaks()
@@ -626,6 +844,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 128^2, 256^3 and 512^3 sub-lines")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy block against the oracle")
     ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C5", "sphere"],
                     help="C2: 1024^2 headline (default); C3: 256^3, C5: 512^3 (FP32 only); "
                          "sphere: the closed-surface workload of Sec. 6.2")

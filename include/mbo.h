@@ -174,6 +174,17 @@ enum {
 MBO_API mbo_status mbo_profile_enable(mbo_handle h, int enable);
 MBO_API mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npass);
 
+/* Throughput of the SIMT fused multiply-add pipes of the current device, in
+ * TFLOP/s (2 flops per multiply-add): FP32 scalar FFMA, FP32 packed pairs
+ * (two multiply-adds per instruction) and FP64 DFMA, each the best of five
+ * timed launches of independent a <- a b + c chains over every SM.  A
+ * measurement utility (the paper has no counterpart): the benchmark states
+ * the FP64 form's ALU roofline against it.  Allocates 64 bytes; synchronous;
+ * changes no clock or power setting.  Errors: MBO_ERR_INVALID_ARG (null
+ * output), MBO_ERR_OOM, MBO_ERR_CUDA. */
+MBO_API mbo_status mbo_measure_fma_peaks(double* fp32_tflops, double* fp32x2_tflops,
+                                         double* fp64_tflops);
+
 /* Diffusion without any device allocation.
  *
  * Same result as mbo_diffuse (A_tilde = e^{tau Lap} A on the grid given by

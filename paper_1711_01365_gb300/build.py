@@ -1,7 +1,10 @@
 """Build the CUDA library ``_build/libmbo_gb300.so`` for sm_103a with nvcc.
 
-The three translation units (host API, FP32 kernels, FP64 kernels) compile in
-parallel; the shared object exports the C ABI of ``include/mbo.h``.
+The translation units (host API, FP32 and FP64 generic kernels, the FP32
+warp-plan x and strided passes, radix select, the allocation-free entry
+point, closed surfaces, the pipe-throughput probe) compile in parallel; the
+shared object exports the C ABI of ``include/mbo.h`` and
+``include/mbo_surface.h``.
 """
 from __future__ import annotations
 
@@ -17,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmbo_gb300.so")
 SOURCES = ["mbo_api.cu", "k_f32.cu", "k_f64.cu", "k_warp.cu", "k_wcol.cu", "k_select.cu", "mbo_noalloc.cu",
-           "mbo_surface.cu"]
+           "mbo_surface.cu", "mbo_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

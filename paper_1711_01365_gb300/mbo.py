@@ -31,7 +31,7 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
            "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_step_volume", "mbo_run_volume",
            "mbo_batch_create", "mbo_batch_destroy",
            "mbo_batch_step", "mbo_batch_run", "mbo_batch_workspace_bytes", "mbo_batch_last_error",
-           "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error")
+           "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error", "mbo_measure_fma_peaks")
 
 SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
                    "mbo_surface_peanut_band",
@@ -113,6 +113,7 @@ def lib():
     L.mbo_profile_enable.argtypes = [vp, C.c_int]
     L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_diffuse_noalloc.argtypes = [C.c_int, i64p, C.c_int, C.c_double, C.c_int, vp, vp, vp]
+    L.mbo_measure_fma_peaks.argtypes = [C.POINTER(C.c_double)] * 3
     L.mbo_step_volume.argtypes = [vp, vp, C.c_int64, C.POINTER(mbo_stats), vp]
     L.mbo_run_volume.argtypes = [vp, vp, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
@@ -280,6 +281,14 @@ def mbo_diffuse_noalloc(dims, n: int, tau: float, dtype: int, A, A_tilde, stream
     d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
     _check(lib().mbo_diffuse_noalloc(len(dims), d, int(n), float(tau), int(dtype), _ptr(A),
                                      _ptr(A_tilde), _stream(stream)))
+
+
+def mbo_measure_fma_peaks() -> dict:
+    """SIMT multiply-add throughput of the current device in TFLOP/s:
+    {"fp32": scalar FFMA, "fp32x2": packed pairs, "fp64": DFMA}."""
+    a, b, c = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check(lib().mbo_measure_fma_peaks(C.byref(a), C.byref(b), C.byref(c)))
+    return {"fp32": a.value, "fp32x2": b.value, "fp64": c.value}
 
 
 def mbo_step_volume(h, A, n_plus: int = -1, want_stats: bool = False, stream=None):

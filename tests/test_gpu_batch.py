@@ -116,7 +116,8 @@ def test_batch_96_uneven_fields_full_size(M):
         Bg = A[i][idx].double().cpu().numpy().T
         s = np.linalg.svd(At_o.reshape(-1, n, n), compute_uv=False)
         cs = s[:, -1] + s[:, -2]
-        ok = (np.prod(s, axis=1) > 1e-4) & (cs >= 0.1)
+        cut = 64 * 2.0 ** -24 * np.sqrt((s ** 2).sum(axis=1)) ** n  # FP32 det rounding level
+        ok = (np.prod(s, axis=1) > cut) & (cs >= 1e-2)
         assert ok.sum() >= 6
         assert np.abs(Bg - B_o).max(axis=1)[ok].max() <= 2e-5
     b.close()

@@ -7,13 +7,17 @@ configuration the benchmark uses (default mbo_config).
   * 256^3, n = 3, tau = 2h^2 (Voronoi rotations + noise) and 512^3, n = 3,
     tau = 2h^2 (smooth SO(3) field with 20% reflections), FP32 form with FP64
     re-projection: the library projects the raw field and takes one step; the
-    oracle computes the same step at sampled points one by one from the raw
+    oracle computes the same step at 10^4 (256^3) and 4000 (512^3) sampled
+    points one by one from the raw
     field (its own projection, the convolution with the periodic heat kernel,
     its own projection).  Properties that hold at any size are checked on every
     point: orthogonality, and an energy that does not increase over steps.
 
 Tolerances are those of test_gpu_parity (max-entry 1e-12 in FP64; in FP32
-2e-5 where sigma_{n-1} + sigma_n >= 0.1, else the condition-number bound).
+2e-5 where sigma_{n-1} + sigma_n >= 1e-2, else the condition-number bound;
+points whose |det A~| is within 64 eps_32 |A~|_F^3 of zero, where an FP32 sign
+decision is rounding noise, are checked for validity only, and their number
+is asserted small).
 """
 import numpy as np
 import pytest
@@ -26,6 +30,8 @@ pytestmark = pytest.mark.gpu
 
 F32_STEP_TOL = 2e-5
 F32_DIFF_TOL = 4e-6
+F32_WELL_CS = 1e-2
+EPS32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -57,6 +63,7 @@ def test_c2_full_field_one_step_matches_oracle(M):
     s = _sv(np.moveaxis(At.reshape(n * n, -1), 0, -1), n)
     cs = (s[:, -1] + s[:, -2]).reshape(dims)
     absdet = np.abs(np.prod(s, axis=1)).reshape(dims)
+    cut32 = (64 * EPS32 * np.sqrt((s ** 2).sum(axis=1)) ** n).reshape(dims)
     for dtype in ("f64", "f32"):
         h = M.Mbo(dims, n, tau, dtype)
         tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -69,8 +76,12 @@ def test_c2_full_field_one_step_matches_oracle(M):
             assert err[unamb].max() <= 1e-12
             assert rec["energy"] == pytest.approx(st["energy"], rel=1e-12)
         else:
-            unamb = absdet > 1e-4
-            well = unamb & (cs >= 0.1)
+            unamb = absdet > cut32
+            excluded = int((~unamb).sum())
+            print(f"C2 f32: {excluded} points with |det| at rounding level, "
+                  f"{int((unamb & (cs < F32_WELL_CS)).sum())} with sigma_2 + sigma_3 < 1e-2")
+            assert excluded <= 1000
+            well = unamb & (cs >= F32_WELL_CS)
             assert err[well].max() <= F32_STEP_TOL
             bound = F32_STEP_TOL + 2 * n * F32_DIFF_TOL / np.maximum(cs, 1e-30)
             assert np.all(err[unamb] <= bound[unamb])
@@ -98,8 +109,9 @@ def _sampled_3d_case(M, name, nsamples, seed):
     cs = s[:, -1] + s[:, -2]
     absdet = np.prod(s, axis=1)
     err = np.abs(B - B_o).max(axis=1)
-    unamb = absdet > 1e-4
-    well = unamb & (cs >= 0.1)
+    unamb = absdet > 64 * EPS32 * np.sqrt((s ** 2).sum(axis=1)) ** n
+    assert int((~unamb).sum()) <= max(2, nsamples // 100)
+    well = unamb & (cs >= F32_WELL_CS)
     assert well.sum() >= nsamples // 2
     assert err[well].max() <= F32_STEP_TOL
     bound = F32_STEP_TOL + 2 * n * F32_DIFF_TOL / np.maximum(cs, 1e-30)
@@ -114,8 +126,8 @@ def _sampled_3d_case(M, name, nsamples, seed):
 
 
 def test_c3_256cube_one_step_sampled_against_oracle(M):
-    _sampled_3d_case(M, "C3", 96, 31)
+    _sampled_3d_case(M, "C3", 10000, 31)
 
 
 def test_c5_512cube_one_step_sampled_against_oracle(M):
-    _sampled_3d_case(M, "C5", 64, 53)
+    _sampled_3d_case(M, "C5", 4000, 53)

@@ -6,10 +6,13 @@ Tolerances (max-entry absolute error; entries of O_n fields are <= 1):
              the sign decision in each side's own arithmetic and are
              excluded from the value comparison, then checked for validity);
   FP32 path  diffusion 4e-6; projection and one step 2e-5 at points whose
-             polar factor is well conditioned (sigma_{n-1} + sigma_n >= 0.1,
-             condition number <= 20), and elsewhere the first-order bound
-             2e-5 + 2 * err(A~) / (sigma_{n-1} + sigma_n) that the polar
+             polar factor is not ill conditioned (sigma_{n-1} + sigma_n >=
+             1e-2, condition number <= 200), and elsewhere the first-order
+             bound 2e-5 + 2 * err(A~) / (sigma_{n-1} + sigma_n) that the polar
              factor's condition number gives; energy relative error 1e-5.
+             Points whose |det A~| is within 64 eps_32 |A~|_F^n of zero, where
+             the single-precision sign decision is rounding noise, are checked
+             for validity only; their number is asserted small.
 """
 import math
 
@@ -61,6 +64,21 @@ def cond_sum(At, n):
 
 def dets(At, n):
     return np.linalg.det(mats(At, n))
+
+
+# FP32 sign decisions: |det A~| within 64 eps_32 |A~|_F^n of zero is rounding
+# noise for a determinant computed in single precision (the FP32 rounding of
+# A~ alone moves det by ~n eps |A~|^n); such points are compared for validity
+# only (reading of Lemma 1.1 at det A~ = 0).
+EPS32 = 2.0 ** -24
+# the strict FP32 bound holds where sigma_{n-1} + sigma_n >= 1e-2 (the polar
+# factor's condition number 2 / (sigma_{n-1} + sigma_n) is at most 200 there)
+F32_WELL_CS = 1e-2
+
+
+def det_cut32(At, n):
+    nrm = np.sqrt((mats(At, n) ** 2).sum(axis=(1, 2)))
+    return 64 * EPS32 * nrm ** n
 
 
 def projected(dims, n, seed):
@@ -135,14 +153,17 @@ def test_project_matches_oracle(M, n, dtype):
     orth = np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(n)).max()
     assert orth < (1e-13 if dtype == "f64" else 2e-6)
     assert np.array_equal(np.sign(np.linalg.det(Bm)).reshape(dims), sg.cpu().numpy().astype(float))
-    unamb = d > (1e-12 if dtype == "f64" else 1e-4)
+    unamb = d > (1e-12 if dtype == "f64" else det_cut32(At, n).reshape(dims))
+    excluded = int((~unamb).sum())
+    print(f"n={n} {dtype}: {excluded} of {unamb.size} points with |det| at rounding level")
+    assert excluded <= max(2, unamb.size // 100)
     assert np.array_equal(sg.cpu().numpy()[unamb], sref[unamb])
     err = np.abs(B - ref).max(axis=0)
     if dtype == "f64":
         assert err[unamb].max() <= F64_TOL
     else:
         cs = cond_sum(At, n).reshape(dims)
-        well = unamb & (cs >= 0.1)
+        well = unamb & (cs >= F32_WELL_CS)
         assert err[well].max() <= F32_STEP_TOL
         eps_in = np.abs(At - At.astype(np.float32).astype(np.float64)).max(axis=0)
         bound = F32_STEP_TOL + 2 * (eps_in * n + 1e-7) / np.maximum(cs, 1e-30)
@@ -209,8 +230,11 @@ def test_one_step_matches_oracle(M, dims, n, dtype):
             assert rec["det_flips"] == st["det_flips"]
     else:
         cs = cond_sum(At, n).reshape(dims)
-        unamb = d > 1e-4
-        well = unamb & (cs >= 0.1)
+        unamb = d > det_cut32(At, n).reshape(dims)
+        excluded = int((~unamb).sum())
+        print(f"{dims} n={n} f32: {excluded} of {unamb.size} points with |det| at rounding level")
+        assert excluded <= max(2, unamb.size // 100)
+        well = unamb & (cs >= F32_WELL_CS)
         assert err[well].max() <= F32_STEP_TOL
         bound = F32_STEP_TOL + 2 * F32_DIFF_TOL * n / np.maximum(cs, 1e-30)
         assert np.all(err[unamb] <= bound[unamb])
@@ -392,7 +416,7 @@ def test_project_small_sigma_min_f32_routes(M):
     Bm = mats(B, 3)
     assert np.abs(np.einsum("pki,pkj->pij", Bm, Bm) - np.eye(3)).max() < 2e-6
     d = np.abs(dets(At, 3)).reshape(dims)
-    unamb = d > 1e-4
+    unamb = d > det_cut32(At, 3).reshape(dims)
     assert unamb.sum() >= 448
     assert np.array_equal(sg.cpu().numpy()[unamb], sref[unamb])
     cs = cond_sum(At, 3).reshape(dims)
