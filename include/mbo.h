@@ -85,6 +85,12 @@ typedef struct {
   int axis_stages;       /* MBO_F32 y / z passes of length 256..2048: tile
                             buffers per block, 1 or 2 (2: the next tile's copy is
                             in flight while a tile is transformed); 0 = automatic. */
+  int autotune;          /* 1: mbo_create times the candidate launch shapes of
+                            this geometry (tile width, tile buffers, threads per
+                            block of the strided and row passes) on a scratch
+                            field and keeps the fastest; the choice is cached
+                            per (dims, n, dtype) for the process.  Fields set
+                            explicitly above are not tuned.  Default 0.        */
 } mbo_config;
 
 /* Per-step record.  Step s maps A_{s} to A_{s+1}. */
@@ -97,6 +103,11 @@ typedef struct {
 } mbo_stats;
 
 MBO_API void mbo_default_config(mbo_config* cfg);
+
+/* The launch shapes a handle uses (after any autotuning): row_threads,
+ * axis_threads, axis_tx and axis_stages filled in; the other fields as the
+ * handle was created with. */
+MBO_API mbo_status mbo_launch_config(mbo_handle h, mbo_config* out);
 
 /* Create a handle for one field geometry.
  *   out   receives the handle (set to NULL on failure).
@@ -173,6 +184,18 @@ enum {
 };
 MBO_API mbo_status mbo_profile_enable(mbo_handle h, int enable);
 MBO_API mbo_status mbo_profile_read(mbo_handle h, double* ms, int64_t* launches, int npass);
+
+/* Self-test of the device-side timeout path (no paper counterpart).  Every
+ * wait inside the library's kernels is bounded; on expiry a kernel sets an
+ * error bit in the handle's device state, gives its copies in flight a bounded
+ * wait and returns, and the next synchronising call reports
+ * MBO_ERR_DEVICE_TIMEOUT (clearing the bit).  This call runs that path on
+ * purpose: one block waits, with the same bounded wait, on an mbarrier phase
+ * that nothing completes, for limit_cycles SM cycles (1 .. 2e9), then returns.
+ * Expected result: MBO_ERR_DEVICE_TIMEOUT, with the handle usable afterwards.
+ * Synchronises stream.  Errors: MBO_ERR_INVALID_ARG (null handle, limit out of
+ * range), MBO_ERR_CUDA. */
+MBO_API mbo_status mbo_selftest_wait_timeout(mbo_handle h, int64_t limit_cycles, void* stream);
 
 /* Throughput of the SIMT fused multiply-add pipes of the current device, in
  * TFLOP/s (2 flops per multiply-add): FP32 scalar FFMA, FP32 packed pairs

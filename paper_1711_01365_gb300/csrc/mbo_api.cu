@@ -10,11 +10,15 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mbo.h"
 #include "mbo_dev.cuh"
 #include "mbo_internal.h"
+#include "mbo_tma.cuh"
 
 namespace mbo {
 
@@ -423,6 +427,171 @@ void invalidate_graph(mbo_ctx* h) {
   h->g_ptr = nullptr;
 }
 
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner.  Candidates: the strided passes' tile width (and, for
+// FP32 warp-plan axes, one or two tile buffers per block; for the in-place
+// network, threads per block), then the row pass's threads per block where
+// the x axis takes the network.  Each candidate runs a fresh step and one
+// more on a scratch field, then three timed steps; the fastest is kept and
+// cached per (dims, n, dtype) for the process.
+// ---------------------------------------------------------------------------
+struct LaunchShape {
+  int tx, stages, axis_threads, row_threads;
+};
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchShape> g_tune_cache;
+
+template <typename R> __global__ void k_tune_fill(R* A, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    A[i] = (R)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);  // uniform in [-1, 1)
+  }
+}
+
+bool shape_fits(mbo_ctx* h, const LaunchShape& c, int maxsm) {
+  const Geom& g = h->g;
+  if (c.tx < 1 || g.nx % c.tx) return false;
+  if (axis_smem_bytes(std::max(g.ny, g.nz), c.tx, h->elem) > (size_t)maxsm) return false;
+  if (h->dtype == MBO_F32) {
+    for (int ax = 1; ax < g.ndim; ++ax) {
+      if (!h->tf.plan[ax].lq) continue;
+      const int L = ax == 1 ? g.ny : g.nz;
+      const int wt = warp_tile(L, g.nx, c.tx);
+      if (!wt || wcol_smem_bytes(L, wt, c.stages) > (size_t)maxsm) return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t apply_shape(mbo_ctx* h, const LaunchShape& c) {
+  h->tx = c.tx;
+  h->axis_stages = c.stages;
+  h->axis_threads = c.axis_threads;
+  h->row_threads = c.row_threads;
+  invalidate_graph(h);
+  const Geom& g = h->g;
+  cudaError_t e = h->dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx, h->axis_stages)
+                                      : prepare_kernels<double>(g, h->td, h->tx, 1);
+  if (e != cudaSuccess) return e;
+  if (h->dtype == MBO_F32) {
+    for (int ax = 1; ax < g.ndim; ++ax) {
+      if (!h->tf.plan[ax].lq) continue;
+      const int L = ax == 1 ? g.ny : g.nz;
+      if (!wcol_tensor_map(&h->wmap[ax], h->W, g, ax, warp_tile(L, g.nx, h->tx)))
+        return cudaErrorInvalidValue;
+      h->wmap_ok[ax] = true;
+    }
+  }
+  return cudaSuccess;
+}
+
+// ms per step of the handle's current launch shapes on field A
+cudaError_t time_shape(mbo_ctx* h, void* A, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                       float& ms) {
+  cudaError_t e = row_pass(h, ROW_FWD, A, nullptr, stats_ptrs(h, true, false, -1.0), s);
+  if (e == cudaSuccess) e = step_passes(h, A, false, -1.0, s);
+  if (e == cudaSuccess) e = step_passes(h, A, false, -1.0, s);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(e0, s);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = step_passes(h, A, false, -1.0, s);
+  cudaEventRecord(e1, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  ms = t / 3.f;
+  return cudaGetLastError();
+}
+
+mbo_status autotune(mbo_ctx* h, int maxsm) {
+  const Geom& g = h->g;
+  const mbo_config& c = h->cfg;
+  const TuneKey key{g.ndim, g.nz, g.ny, g.nx, g.n, (int)h->dtype};
+  LaunchShape best{h->tx, h->axis_stages, h->axis_threads, h->row_threads};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      LaunchShape sh = it->second;
+      if (c.axis_tx) sh.tx = h->tx;
+      if (c.axis_stages) sh.stages = h->axis_stages;
+      if (c.axis_threads) sh.axis_threads = h->axis_threads;
+      if (c.row_threads) sh.row_threads = h->row_threads;
+      return apply_shape(h, sh) == cudaSuccess ? MBO_OK : MBO_ERR_CUDA;
+    }
+  }
+  const bool f32 = h->dtype == MBO_F32;
+  bool warp_axis = false, net_axis = false;
+  for (int ax = 1; ax < g.ndim; ++ax) {
+    if (f32 && h->tf.plan[ax].lq) warp_axis = true;
+    else net_axis = true;
+  }
+  const bool net_row = !(f32 && h->tf.plan[0].lq);
+  std::vector<int> txs, stages, athreads, rthreads;
+  for (int t : {h->tx, h->tx / 2, 4})
+    if (t >= 1 && std::find(txs.begin(), txs.end(), t) == txs.end()) txs.push_back(t);
+  if (c.axis_tx) txs = {h->tx};
+  stages = (warp_axis && !c.axis_stages) ? std::vector<int>{1, 2} : std::vector<int>{h->axis_stages};
+  athreads = (net_axis && !c.axis_threads) ? std::vector<int>{128, 256, 384}
+                                           : std::vector<int>{h->axis_threads};
+  rthreads = (net_row && !c.row_threads) ? std::vector<int>{64, 128, 192, 256, 384}
+                                         : std::vector<int>{h->row_threads};
+  const size_t fbytes = (size_t)g.C * (size_t)g.P * h->elem;
+  void* A = nullptr;
+  if (cudaMalloc(&A, fbytes) != cudaSuccess) return MBO_ERR_OOM;
+  cudaStream_t s = h->cap;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = cudaSuccess;
+  const long long nv = (long long)g.C * g.P;
+  if (f32) {
+    k_tune_fill<float><<<256, 256, 0, s>>>(static_cast<float*>(A), nv);
+    e = launch_project<float>(g, static_cast<float*>(A), static_cast<float*>(A), nullptr, 0.0, s);
+  } else {
+    k_tune_fill<double><<<256, 256, 0, s>>>(static_cast<double*>(A), nv);
+    e = launch_project<double>(g, static_cast<double*>(A), static_cast<double*>(A), nullptr, 0.0, s);
+  }
+  float best_ms = 1e30f;
+  auto consider = [&](const LaunchShape& sh) {
+    if (e != cudaSuccess || !shape_fits(h, sh, maxsm)) return;
+    if ((e = apply_shape(h, sh)) != cudaSuccess) return;
+    float ms = 0.f;
+    if ((e = time_shape(h, A, s, e0, e1, ms)) != cudaSuccess) return;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sh;
+    }
+  };
+  // strided passes first (row threads at their default), then the row pass
+  const LaunchShape start = best;
+  for (int t : txs)
+    for (int st : stages)
+      for (int at : athreads) consider(LaunchShape{t, st, at, start.row_threads});
+  const LaunchShape mid = best;
+  for (int rt : rthreads)
+    if (rt != mid.row_threads) consider(LaunchShape{mid.tx, mid.stages, mid.axis_threads, rt});
+  if (e == cudaSuccess) e = apply_shape(h, best);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(A);
+  if (e == cudaSuccess)
+    e = cudaMemset(h->st, 0, sizeof(RunState)) == cudaSuccess &&
+                cudaMemset(h->hist_mem, 0, (size_t)kRing * 5 * sizeof(double)) == cudaSuccess
+            ? cudaSuccess
+            : cudaErrorUnknown;
+  h->w_valid_for = nullptr;
+  if (e != cudaSuccess) return MBO_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return MBO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -451,6 +620,7 @@ void mbo_default_config(mbo_config* cfg) {
   cfg->axis_threads = 0;
   cfg->axis_tx = 0;
   cfg->axis_stages = 0;
+  cfg->autotune = 0;
 }
 
 int64_t mbo_workspace_bytes(mbo_handle h) { return h ? (int64_t)h->bytes_total : 0; }
@@ -582,6 +752,8 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   };
   const size_t wbytes = (size_t)g.Q * (size_t)g.P * 2 * h->elem;
   const int rows = g.nz * g.ny;
+  // the autotuner may narrow the column tiles (down to half, or 4 columns)
+  if (c.autotune && !c.axis_tx) min_tx = std::max(1, std::min(min_tx, std::min(h->tx / 2, 4)));
   const int tiles = g.Q * std::max(g.nz, g.ny) * (g.nx / min_tx);
   const size_t nparts = (size_t)std::max(rows, tiles);
   h->ngroups = (nparts + kReduceGroup - 1) / kReduceGroup;
@@ -639,7 +811,24 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     mbo_destroy(h);
     return MBO_ERR_CUDA;
   }
+  if (c.autotune) {
+    const mbo_status ts = autotune(h, maxsm);
+    if (ts != MBO_OK) {
+      mbo_destroy(h);
+      return ts;
+    }
+  }
   *out = h;
+  return MBO_OK;
+}
+
+mbo_status mbo_launch_config(mbo_handle h, mbo_config* out) {
+  if (!h || !out) return MBO_ERR_INVALID_ARG;
+  *out = h->cfg;
+  out->row_threads = h->row_threads;
+  out->axis_threads = h->axis_threads;
+  out->axis_tx = h->tx;
+  out->axis_stages = h->axis_stages;
   return MBO_OK;
 }
 
@@ -693,6 +882,21 @@ static mbo_status read_record(mbo_handle h, long long slot, mbo_stats* out) {
   return MBO_OK;
 }
 
+// Self-test of the bounded-wait error path: one block waits on an mbarrier
+// phase that nothing completes (no arrival, no copy), with the same bounded
+// wait the TMA passes use, and records the timeout in the run state's error
+// word as they do.
+__global__ void k_wait_timeout_selftest(RunState* st, long long limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, limit)) != 0;
+  if (!ok && threadIdx.x == 0) atomicOr(&st->err, kErrWaitTimeout);
+}
+
 // Device error bits of the last synchronised read of the run state: a
 // kernel whose bounded wait gave up left them set.  The bits are cleared so
 // that later calls start clean.
@@ -723,6 +927,17 @@ mbo_status mbo_step(mbo_handle h, void* A, int flags, mbo_stats* stats, void* st
     if (stats->nonfinite) return fail(h, MBO_ERR_NUMERIC, "%lld non-finite points", (long long)stats->nonfinite);
   }
   return MBO_OK;
+}
+
+mbo_status mbo_selftest_wait_timeout(mbo_handle h, int64_t limit_cycles, void* stream) {
+  if (!h || limit_cycles < 1 || limit_cycles > kWaitCycles) return MBO_ERR_INVALID_ARG;
+  DeviceGuard dg(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_wait_timeout_selftest<<<1, 64, 0, s>>>(h->st, (long long)limit_cycles);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(h->h_st, h->st, sizeof(RunState), cudaMemcpyDeviceToHost));
+  return device_errors(h);
 }
 
 mbo_status mbo_lyapunov(mbo_handle h, const void* A, double* E, void* stream) {

@@ -31,7 +31,8 @@ EXPORTS = ("mbo_default_config", "mbo_create", "mbo_destroy", "mbo_diffuse", "mb
            "mbo_profile_read", "mbo_diffuse_noalloc", "mbo_step_volume", "mbo_run_volume",
            "mbo_batch_create", "mbo_batch_destroy",
            "mbo_batch_step", "mbo_batch_run", "mbo_batch_workspace_bytes", "mbo_batch_last_error",
-           "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error", "mbo_measure_fma_peaks")
+           "mbo_workspace_bytes", "mbo_status_string", "mbo_last_error", "mbo_measure_fma_peaks",
+           "mbo_selftest_wait_timeout", "mbo_launch_config")
 
 SURFACE_EXPORTS = ("mbo_surface_band_width", "mbo_surface_heat_modes", "mbo_surface_sphere_band",
                    "mbo_surface_peanut_band",
@@ -58,7 +59,10 @@ class MboError(RuntimeError):
 class mbo_config(C.Structure):
     _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int),
                 ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int),
-                ("axis_stages", C.c_int)]
+                ("axis_stages", C.c_int), ("autotune", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class mbo_surface_params(C.Structure):
@@ -114,6 +118,8 @@ def lib():
     L.mbo_profile_read.argtypes = [vp, C.POINTER(C.c_double), i64p, C.c_int]
     L.mbo_diffuse_noalloc.argtypes = [C.c_int, i64p, C.c_int, C.c_double, C.c_int, vp, vp, vp]
     L.mbo_measure_fma_peaks.argtypes = [C.POINTER(C.c_double)] * 3
+    L.mbo_selftest_wait_timeout.argtypes = [vp, C.c_int64, vp]
+    L.mbo_launch_config.argtypes = [vp, C.POINTER(mbo_config)]
     L.mbo_step_volume.argtypes = [vp, vp, C.c_int64, C.POINTER(mbo_stats), vp]
     L.mbo_run_volume.argtypes = [vp, vp, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
@@ -281,6 +287,19 @@ def mbo_diffuse_noalloc(dims, n: int, tau: float, dtype: int, A, A_tilde, stream
     d = (C.c_int64 * len(dims))(*[int(v) for v in dims])
     _check(lib().mbo_diffuse_noalloc(len(dims), d, int(n), float(tau), int(dtype), _ptr(A),
                                      _ptr(A_tilde), _stream(stream)))
+
+
+def mbo_launch_config(h) -> dict:
+    """The launch shapes the handle uses (after any autotuning)."""
+    c = mbo_config()
+    _check(lib().mbo_launch_config(h, C.byref(c)), h)
+    return c.as_dict()
+
+
+def mbo_selftest_wait_timeout(h, limit_cycles: int = 2_000_000, stream=None) -> int:
+    """Run the bounded-wait timeout path on purpose (see include/mbo.h); returns
+    the status code (MBO_ERR_DEVICE_TIMEOUT = 6 when the path works)."""
+    return int(lib().mbo_selftest_wait_timeout(h, int(limit_cycles), _stream(stream)))
 
 
 def mbo_measure_fma_peaks() -> dict:

@@ -70,3 +70,8 @@ def test_default_config(lib):
     c = M.mbo_default_config()
     assert c.fallback_sigma == 0.0
     assert c.check_interval == 16 and c.use_graph == 1
+
+
+def test_timeout_selftest_rejects_bad_arguments_without_a_device(lib):
+    # a null handle or a limit outside 1 .. 2e9 cycles is refused before any device call
+    assert lib.mbo_selftest_wait_timeout(None, 1000, None) == 1

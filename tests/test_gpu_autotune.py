@@ -1,0 +1,103 @@
+"""The launch-shape autotuner (mbo_config.autotune).
+
+A tuned handle picks its strided-pass tile width, tile buffers, threads per
+block of the network passes and of the network row pass by timing candidate
+steps on a scratch field.  Launch shapes only decide which block computes
+which column or row: the arithmetic of every point is the same, so the field
+after a step must equal the default handle's bit for bit, and the FP64 energy
+may differ only by the order of its block sums.  A second handle of the same
+(dims, n, dtype) takes the cached choice.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1711_01365_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1711_01365_gb300 import build
+    build.build()
+    from paper_1711_01365_gb300 import mbo
+    return mbo
+
+
+CASES = [((1024, 1024), 3, "f32"), ((384, 384), 2, "f32"), ((256, 512), 3, "f32"),
+         ((96, 64), 2, "f64"), ((16, 24, 32), 3, "f32")]
+
+
+@pytest.mark.parametrize("dims,n,dtype", CASES)
+def test_tuned_step_equals_default_step(M, dims, n, dtype):
+    tau = 3.0 / max(dims) ** 2
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    A0 = torch.tensor(O.project(I.gaussian(dims, n, 5), n), dtype=tdt, device="cuda")
+    hd = M.Mbo(dims, n, tau, dtype)
+    ht = M.Mbo(dims, n, tau, dtype, autotune=1)
+    cd, ct = M.mbo_launch_config(hd.h), M.mbo_launch_config(ht.h)
+    assert ct["autotune"] == 1 and cd["autotune"] == 0
+    nx = dims[-1]
+    assert ct["axis_tx"] >= 1 and nx % ct["axis_tx"] == 0
+    assert ct["axis_stages"] in (1, 2)
+    assert 64 <= ct["row_threads"] <= 384 and ct["row_threads"] % 32 == 0
+    assert 64 <= ct["axis_threads"] <= 384 and ct["axis_threads"] % 32 == 0
+    Ad, At = A0.clone(), A0.clone()
+    for k in range(3):
+        fl = 0 if k == 0 else M.MBO_STEP_CONTINUE
+        rd = hd.step(Ad, flags=fl, want_stats=True)
+        rt = ht.step(At, flags=fl, want_stats=True)
+        torch.cuda.synchronize()
+        assert torch.equal(Ad, At), f"step {k}: tuned launch shapes changed the field"
+        assert rd["det_flips"] == rt["det_flips"]
+        assert rd["fallback_points"] == rt["fallback_points"]
+        assert abs(rd["energy"] - rt["energy"]) <= 1e-12 * abs(rd["energy"])
+    # the choice is cached for the process
+    h2 = M.Mbo(dims, n, tau, dtype, autotune=1)
+    assert M.mbo_launch_config(h2.h) == ct
+    for h in (hd, ht, h2):
+        h.close()
+
+
+def test_tuned_run_matches_oracle(M):
+    dims, n = (128, 96), 2
+    tau = 4.0 / 128 ** 2
+    A0 = O.project(I.gaussian(dims, n, 11), n)
+    h = M.Mbo(dims, n, tau, "f64", autotune=1)
+    A = torch.tensor(A0, dtype=torch.float64, device="cuda")
+    res = h.run(A, 40, 1e-10)
+    ref, info = O.run(A0, n, tau, 40, 1e-10)
+    # the tuning steps left no trace in the run state: step count and energies
+    assert res["steps"] == info["steps"] and res["stationary"] == info["stationary"]
+    np.testing.assert_allclose(res["energies"], info["energies"], rtol=1e-10)
+    np.testing.assert_allclose(A.cpu().numpy(), ref, atol=1e-10, rtol=0)
+    h.close()
+
+
+def test_explicit_shape_is_kept(M):
+    dims, n = (512, 512), 3
+    h = M.Mbo(dims, n, 3.0 / 512 ** 2, "f32", autotune=1, axis_tx=4, axis_stages=1)
+    c = M.mbo_launch_config(h.h)
+    assert c["axis_tx"] == 4 and c["axis_stages"] == 1
+    h.close()
+
+
+def test_batch_with_autotune_equals_default_batch(M):
+    spec = [((256, 256), 2), ((384, 384), 3), ((512, 512), 3)]
+    taus = [4.0 / d[0] ** 2 for d, _ in spec]
+    A = [torch.tensor(O.project(I.gaussian(d, n, 20 + k), n), dtype=torch.float32, device="cuda")
+         for k, (d, n) in enumerate(spec)]
+    B = [a.clone() for a in A]
+    bd = M.Batch([d for d, _ in spec], [n for _, n in spec], taus, "f32")
+    bt = M.Batch([d for d, _ in spec], [n for _, n in spec], taus, "f32", autotune=1)
+    for k in range(2):
+        fl = 0 if k == 0 else M.MBO_STEP_CONTINUE
+        bd.step(A, flags=fl)
+        bt.step(B, flags=fl)
+    torch.cuda.synchronize()
+    for a, b in zip(A, B):
+        assert torch.equal(a, b)
+    bd.close()
+    bt.close()
