@@ -87,10 +87,16 @@ typedef struct {
                             in flight while a tile is transformed); 0 = automatic. */
   int autotune;          /* 1: mbo_create times the candidate launch shapes of
                             this geometry (tile width, tile buffers, threads per
-                            block of the strided and row passes) on a scratch
+                            block of the strided and row passes, dependent
+                            launch) on a scratch
                             field and keeps the fastest; the choice is cached
                             per (dims, n, dtype) for the process.  Fields set
                             explicitly above are not tuned.  Default 0.        */
+  int pdl;               /* MBO_F32 warp-plan passes: programmatic dependent
+                            launch, each pass scheduled while the one before it
+                            finishes.  1 = on, 2 = off, 0 = automatic (on where
+                            the x pass runs in at most two waves of blocks;
+                            tuned when autotune is set).                        */
 } mbo_config;
 
 /* Per-step record.  Step s maps A_{s} to A_{s+1}. */
@@ -105,8 +111,8 @@ typedef struct {
 MBO_API void mbo_default_config(mbo_config* cfg);
 
 /* The launch shapes a handle uses (after any autotuning): row_threads,
- * axis_threads, axis_tx and axis_stages filled in; the other fields as the
- * handle was created with. */
+ * axis_threads, axis_tx, axis_stages and pdl (1 on, 2 off) filled in; the
+ * other fields as the handle was created with. */
 MBO_API mbo_status mbo_launch_config(mbo_handle h, mbo_config* out);
 
 /* Create a handle for one field geometry.

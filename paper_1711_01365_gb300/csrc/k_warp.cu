@@ -11,6 +11,7 @@
 // Data layout in HBM is that of the generic passes (mbo_kernels.cuh); spectra
 // along these axes are in natural order.
 #include "mbo_kernels.cuh"
+#include "mbo_tma.cuh"
 #include "mbo_wfft.cuh"
 #include "mbo_wshape.cuh"
 
@@ -20,7 +21,7 @@ namespace {
 template <int NM, int MODE, int N>
 __global__ void __launch_bounds__(wrow_threads(N, NM), wrow_minb(N, NM))
 k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2* W, StatsPtrs sp,
-       float fb_sigma) {
+       float fb_sigma, int ahead) {
   constexpr int R = w_r(N), M = w_m(N), LQ = w_lq(N), RB = wrow_rb(N);
   using F = WarpFFTR<M, LQ, R>;
   constexpr int C = NM * NM, Q = (C + 1) / 2, E = F::E, RS = F::RS, NT = wrow_threads(N, NM);
@@ -29,7 +30,9 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   __shared__ double redd[32];
   __shared__ int redi[32];
   __shared__ int s_flag, s_nfb;
+  pdl_wait();  // the previous pass's spectrum and run state are complete
   if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
+  pdl_release();
 
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int tid = threadIdx.x;
@@ -45,6 +48,22 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   const float2* tw = static_cast<const float2*>(t.tw[0]);
   const float2* twr = tw + M;
   float2 v[E];
+  // the forward spectrum of this sequence to W; the last plane of an odd
+  // channel count is Hermitian: columns k < xh only
+  auto store_spectrum = [&](const float2(&u)[E]) {
+    if (!live) return;
+    float2* wdst = W + q * P + off;
+    if (q < Q - 1 || g.xh == N) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) wdst[l + M * r + LQ * j] = u[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int k = l + LQ * j + M * r;
+        if (k < g.xh) wdst[k] = u[j];
+      }
+    }
+  };
 
   if (MODE == ROW_FWD) {
     // per point: load all channels, accumulate n - |A|^2, park the planes
@@ -69,13 +88,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     if constexpr (R > 1) __syncthreads();  // regions are shared across groups
     else __syncwarp();
     F::fwd(v, base, r, tw, twr, l);
-    if (live) {
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int k = l + LQ * j + M * r;
-        if (q < Q - 1 || k < g.xh) W[q * P + off + k] = v[j];
-      }
-    }
+    store_spectrum(v);
     if (sp.do_stats) {
       const double tot = block_sum(defect, redd);
       double all;
@@ -84,22 +97,39 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     return;
   }
 
+  if (MODE == ROW_INV_PROJECT_FWD && tid < C) {
+    // the old field of this block's rows, wanted after the inverse transform
+    const long long nr = rows - row0 < RB ? rows - row0 : RB;
+    bulk_prefetch_l2(A + tid * P + row0 * N, (unsigned)(nr * N * sizeof(float)));
+  } else if (ahead > 0 && tid >= 32 && tid < 32 + RB * Q) {
+    // the spectrum rows of a block of a later wave
+    const long long rn = row0 + (long long)ahead * RB + (tid - 32) / Q;
+    const int qq = (tid - 32) % Q;
+    if (rn < rows) {
+      const int cols = qq == Q - 1 ? g.xh : N;
+      bulk_prefetch_l2(W + qq * P + rn * N, (unsigned)((cols * sizeof(float2) + 15) & ~15u));
+    }
+  }
+
   // inverse modes: the spectrum rows straight into registers (coalesced); a
   // Hermitian last plane supplies columns k > N/2 as conj(column N - k)
   const bool mirror = q == Q - 1 && g.xh < N;
+  const float2* wrow = W + q * P + off;  // this sequence's spectrum row
+  if (!live) {
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int k = l + LQ * j + M * r;
-    float2 z = float2{0.f, 0.f};
-    if (live) {
-      if (mirror && 2 * k > N) {
-        z = W[q * P + off + (N - k)];
-        z.y = -z.y;
-      } else {
-        z = W[q * P + off + k];
-      }
+    for (int j = 0; j < E; ++j) v[j] = float2{0.f, 0.f};
+  } else if (!mirror) {  // warp-uniform: one address per element, constant offsets
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = wrow[l + M * r + LQ * j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int k = l + LQ * j + M * r;
+      const bool up = 2 * k > N;
+      float2 z = wrow[up ? N - k : k];
+      z.y = up ? -z.y : z.y;
+      v[j] = z;
     }
-    v[j] = z;
   }
   F::inv(v, base, r, tw, twr, l);
 
@@ -127,11 +157,16 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   for (int p = tid; p < RB * N; p += NT) {
     const int rw = p / N, x = p - rw * N;
     if (row0 + rw >= rows) continue;
+    // issued first, used last: the loads overlap the projection (the rows
+    // were prefetched to L2 at the start of the block)
+    float old[C];
+    {
+      const float* src = A + (row0 + rw) * N + x;
+#pragma unroll
+      for (int c = 0; c < C; ++c, src += P) old[c] = *src;
+    }
     const long long ro = (row0 + rw) * N;
     float2* pt = sm + rw * Q * PS + x;
-    float old[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) old[c] = A[c * P + ro + x];
     float m[C];
 #pragma unroll
     for (int qq = 0; qq < Q; ++qq) {
@@ -139,9 +174,17 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
       m[2 * qq] = z.x;
       if (2 * qq + 1 < C) m[2 * qq + 1] = z.y;
     }
-    bool fin = true;
+    // finite entries have a finite sum of squares (up to overflow, which
+    // the entry-wise test below settles)
+    float nx = 0.f;
 #pragma unroll
-    for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+    for (int c = 0; c < C; ++c) nx += m[c] * m[c];
+    bool fin = isfinite(nx);
+    if (!fin) {
+      fin = true;
+#pragma unroll
+      for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+    }
     ps.nonfinite += fin ? 0 : 1;
     float b[C];
     float sg;
@@ -183,13 +226,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   if constexpr (R > 1) __syncthreads();
   else __syncwarp();
   F::fwd(v, base, r, tw, twr, l);
-  if (live) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int k = l + LQ * j + M * r;
-      if (q < Q - 1 || k < g.xh) W[q * P + off + k] = v[j];
-    }
-  }
+  store_spectrum(v);
   if (!sp.do_stats) return;
   finalize_step_stats(g.P, g.tau, sp, ps, redd, redi, &s_flag);
 }
@@ -199,14 +236,25 @@ cudaError_t wrow_nm(const Geom& g, const Tables<float>& t, const float* Ain, flo
                     const StatsPtrs& sp, float fb, cudaStream_t s, bool prepare_only) {
   auto k = k_wrow<NM, MODE, N>;
   static size_t done = 0;
+  static int resident = 0;  // blocks of this kernel that fit on the device at once
   const size_t smem = wrow_smem_bytes(g, N, MODE == ROW_INV_PROJECT_FWD);
   cudaError_t e = set_smem_once(k, smem, done);
-  if (e != cudaSuccess || prepare_only) return e;
+  if (e != cudaSuccess) return e;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, wrow_threads(N, NM), smem);
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (prepare_only) return cudaSuccess;
   constexpr int RB = wrow_rb(N);
   const long long rows = g.P / N;
   const int blocks = (int)((rows + RB - 1) / RB);
-  k<<<blocks, wrow_threads(N, NM), smem, s>>>(g, t, Ain, A, static_cast<float2*>(W), sp, fb);
-  return cudaGetLastError();
+  // a block prefetches the spectrum rows of the block one wave later
+  const int ahead = blocks > resident ? resident : 0;
+  return launch_pdl(k, blocks, wrow_threads(N, NM), smem, s, g, t, Ain, A, static_cast<float2*>(W), sp,
+                    fb, ahead);
 }
 
 template <int N>
@@ -239,6 +287,45 @@ size_t wrow_smem_bytes(const Geom& g, int N, bool fallback) {
   size_t b = (size_t)RB * g.Q * R * rs * sizeof(float2);
   if (fallback) b += (size_t)kFallbackCap * ((size_t)g.C * sizeof(float) + sizeof(int));
   return (b + 15) & ~(size_t)15;
+}
+
+namespace {
+template <int NM, int N> double wrow_waves_nm(const Geom& g) {
+  auto k = k_wrow<NM, ROW_INV_PROJECT_FWD, N>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = wrow_smem_bytes(g, N, true);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, wrow_threads(N, NM), smem);
+  const double blocks = (double)((g.P / N + wrow_rb(N) - 1) / wrow_rb(N));
+  return blocks / ((double)sms * (per_sm > 0 ? per_sm : 1));
+}
+template <int N> double wrow_waves_n(const Geom& g) {
+  switch (g.n) {
+    case 1: return wrow_waves_nm<1, N>(g);
+    case 2: return wrow_waves_nm<2, N>(g);
+    case 3: return wrow_waves_nm<3, N>(g);
+    default: return wrow_waves_nm<4, N>(g);
+  }
+}
+}  // namespace
+
+double wrow_waves(const Geom& g) {
+  switch (g.nx) {
+    case 2048: return wrow_waves_n<2048>(g);
+    case 1536: return wrow_waves_n<1536>(g);
+    case 1024: return wrow_waves_n<1024>(g);
+    case 768: return wrow_waves_n<768>(g);
+    case 512: return wrow_waves_n<512>(g);
+    case 256: return wrow_waves_n<256>(g);
+    default: return 0.0;
+  }
+}
+
+bool& pdl_flag() {
+  thread_local bool on = true;
+  return on;
 }
 
 cudaError_t launch_wrow(RowMode mode, const Geom& g, const Tables<float>& t, const float* Ain,

@@ -57,7 +57,6 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
   __shared__ double redd[32];
   __shared__ int s_flag;
   __shared__ __align__(8) unsigned long long bar[NBUF];
-  if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
 
   // 1024-byte aligned tile buffers (the TMA swizzle works on address bits
   // 4..9); offsetting the shared array itself keeps every access below a
@@ -100,7 +99,21 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
 #pragma unroll
     for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
     fence_barrier_init();
-    // the first tiles' loads go out before the tables are staged
+  }
+  {  // the tables are the handle's own: staged while the previous pass finishes
+    const float2* tw = static_cast<const float2*>(t.tw[axis]);
+    for (int i = tid; i < L; i += NT) {
+      s_tw[i] = tw[i];
+      if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
+        s_g[i] = t.g[axis][i];
+        s_om[i] = t.om[axis][i];
+      }
+    }
+  }
+  pdl_wait();  // the previous pass's spectrum and run state are complete
+  if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
+  pdl_release();
+  if (tid == 0) {
     for (int k = 0; k < NBUF && blockIdx.x + k * gridDim.x < ntiles; ++k)
       issue_load(blockIdx.x + k * gridDim.x, k);
     if (blockIdx.x + NBUF * gridDim.x < ntiles) prefetch_tile(blockIdx.x + NBUF * gridDim.x);
@@ -112,16 +125,6 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
       for (long long o = beg; o < end; o += 65536) {
         const long long n = end - o < 65536 ? end - o : 65536;
         bulk_prefetch_l2(pf + o, (unsigned)(n & ~15LL));
-      }
-    }
-  }
-  {
-    const float2* tw = static_cast<const float2*>(t.tw[axis]);
-    for (int i = tid; i < L; i += NT) {
-      s_tw[i] = tw[i];
-      if (MODE == AXIS_FGI || MODE == AXIS_ENERGY) {
-        s_g[i] = t.g[axis][i];
-        s_om[i] = t.om[axis][i];
       }
     }
   }
@@ -267,9 +270,8 @@ cudaError_t wcol_m(const Geom& g, const Tables<float>& t, const CUtensorMap* tm,
   const int nouter = axis == 1 ? g.nz : g.ny;
   const int tiles = col_tiles(g, nouter, TX);
   const int blocks = tiles < slots ? tiles : slots;
-  k<<<blocks, WcolShape<L, TX>::NT, smem, s>>>(g, t, *tm, sp, axis, tiles,
-                                                static_cast<const char*>(pf), pf ? pf_bytes : 0);
-  return cudaGetLastError();
+  return launch_pdl(k, blocks, WcolShape<L, TX>::NT, smem, s, g, t, *tm, sp, axis, tiles,
+                    static_cast<const char*>(pf), pf ? pf_bytes : 0LL);
 }
 
 struct L2Hint {

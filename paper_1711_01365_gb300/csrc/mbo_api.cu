@@ -168,6 +168,7 @@ struct mbo_ctx {
   Tables<double> td{};
   int row_threads = 256, axis_threads = 256, tx = 8;
   int axis_stages = 1;  // tile buffers per block of the FP32 warp-plan strided passes
+  bool pdl = false;     // programmatic dependent launch of the FP32 warp-plan passes
   // TMA descriptors of W for the FP32 warp-plan strided passes (index = axis)
   CUtensorMap wmap[3];
   bool wmap_ok[3] = {false, false, false};
@@ -362,6 +363,7 @@ cudaError_t axis_pass(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp, 
 
 cudaError_t row_launch(mbo_ctx* h, RowMode mode, const void* Ain, void* Aout, const StatsPtrs& sp,
                        cudaStream_t s) {
+  pdl_flag() = h->pdl;
   if (h->dtype == MBO_F32)
     return launch_row<float>(mode, h->g, h->tf, static_cast<const float*>(Ain),
                              static_cast<float*>(Aout), h->W, sp, h->cfg.fallback_sigma,
@@ -380,6 +382,7 @@ cudaError_t axis_launch(mbo_ctx* h, AxisMode mode, int axis, const StatsPtrs& sp
   const size_t abytes = (size_t)h->g.C * (size_t)h->g.P * h->elem;
   const size_t wbytes = (size_t)h->g.Q * (size_t)h->g.P * 2 * h->elem;
   if (abytes + wbytes > kL2HintBytes) l2_hint = nullptr;
+  pdl_flag() = h->pdl;
   if (h->dtype == MBO_F32)
     return launch_axis<float>(mode, axis, h->g, h->tf, h->W, sp, h->tx, h->axis_threads, s,
                               h->wmap_ok[axis] ? &h->wmap[axis] : nullptr, h->axis_stages,
@@ -437,6 +440,7 @@ void invalidate_graph(mbo_ctx* h) {
 // ---------------------------------------------------------------------------
 struct LaunchShape {
   int tx, stages, axis_threads, row_threads;
+  bool pdl;
 };
 using TuneKey = std::tuple<int, int, int, int, int, int>;
 std::mutex g_tune_mu;
@@ -473,6 +477,7 @@ cudaError_t apply_shape(mbo_ctx* h, const LaunchShape& c) {
   h->axis_stages = c.stages;
   h->axis_threads = c.axis_threads;
   h->row_threads = c.row_threads;
+  h->pdl = c.pdl;
   invalidate_graph(h);
   const Geom& g = h->g;
   cudaError_t e = h->dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx, h->axis_stages)
@@ -512,7 +517,7 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   const Geom& g = h->g;
   const mbo_config& c = h->cfg;
   const TuneKey key{g.ndim, g.nz, g.ny, g.nx, g.n, (int)h->dtype};
-  LaunchShape best{h->tx, h->axis_stages, h->axis_threads, h->row_threads};
+  LaunchShape best{h->tx, h->axis_stages, h->axis_threads, h->row_threads, h->pdl};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -522,6 +527,7 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
       if (c.axis_stages) sh.stages = h->axis_stages;
       if (c.axis_threads) sh.axis_threads = h->axis_threads;
       if (c.row_threads) sh.row_threads = h->row_threads;
+      if (c.pdl) sh.pdl = h->pdl;
       return apply_shape(h, sh) == cudaSuccess ? MBO_OK : MBO_ERR_CUDA;
     }
   }
@@ -572,10 +578,15 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   const LaunchShape start = best;
   for (int t : txs)
     for (int st : stages)
-      for (int at : athreads) consider(LaunchShape{t, st, at, start.row_threads});
+      for (int at : athreads) consider(LaunchShape{t, st, at, start.row_threads, start.pdl});
   const LaunchShape mid = best;
   for (int rt : rthreads)
-    if (rt != mid.row_threads) consider(LaunchShape{mid.tx, mid.stages, mid.axis_threads, rt});
+    if (rt != mid.row_threads) consider(LaunchShape{mid.tx, mid.stages, mid.axis_threads, rt, mid.pdl});
+  if (!c.pdl && f32 && !net_row) {  // programmatic dependent launch on or off
+    LaunchShape alt = best;
+    alt.pdl = !alt.pdl;
+    consider(alt);
+  }
   if (e == cudaSuccess) e = apply_shape(h, best);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -621,6 +632,7 @@ void mbo_default_config(mbo_config* cfg) {
   cfg->axis_tx = 0;
   cfg->axis_stages = 0;
   cfg->autotune = 0;
+  cfg->pdl = 0;
 }
 
 int64_t mbo_workspace_bytes(mbo_handle h) { return h ? (int64_t)h->bytes_total : 0; }
@@ -722,6 +734,14 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     }
     h->axis_threads = c.axis_threads;
   }
+  if (c.pdl < 0 || c.pdl > 2) {
+    delete h;
+    return MBO_ERR_INVALID_ARG;
+  }
+  // programmatic dependent launch: measured to help where the projecting x
+  // pass runs in at most two waves of blocks, and to cost a little beyond
+  if (dtype == MBO_F32 && axis_plan(g, 0, true).lq)
+    h->pdl = c.pdl == 1 || (c.pdl == 0 && wrow_waves(g) <= 2.0);
   size_t rs = row_smem_bytes(g, h->elem, true);
   size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
   int min_tx = h->tx;  // narrowest column tile of any strided pass
@@ -829,6 +849,7 @@ mbo_status mbo_launch_config(mbo_handle h, mbo_config* out) {
   out->axis_threads = h->axis_threads;
   out->axis_tx = h->tx;
   out->axis_stages = h->axis_stages;
+  out->pdl = h->pdl ? 1 : 2;
   return MBO_OK;
 }
 

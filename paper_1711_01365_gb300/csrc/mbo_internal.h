@@ -210,6 +210,8 @@ int plan_twiddles(const Plan& p);
 int pick_tx(int nx, int cap);
 
 // FP32 passes over warp-plan axes (k_warp.cu).
+bool& pdl_flag();  // programmatic dependent launch of these passes (per host thread)
+double wrow_waves(const Geom& g);  // waves of blocks of the projecting x pass
 bool warp_plan_length(int N);
 int warp_plan_radix(int N);
 int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4 or 8; 0: none)

@@ -183,12 +183,43 @@ template <typename R>
 __device__ __forceinline__ void finalize_step_stats(long long P, double tau, const StatsPtrs& sp,
                                                     const PointStats<R>& ps, double* redd, int* redi,
                                                     int* s_flag) {
-  const int tid = threadIdx.x;
-  const double dsum = block_sum((double)ps.defect, redd);
-  const double mx = block_max((double)ps.maxd, redd);
-  const int fl = block_sum(ps.flips, redi);
-  const int nfin = block_sum(ps.nonfinite, redi);
-  const int nfb = block_sum(ps.fallback, redi);
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  // one fused block reduction (blocks of at most 16 warps): the defect sum,
+  // the largest change, and the three counts in 21-bit fields of one integer
+  // (a block holds far fewer than 2^21 points)
+  double dsum = (double)ps.defect, mx = (double)ps.maxd;
+  unsigned long long cnt = (unsigned long long)ps.flips |
+                           ((unsigned long long)ps.nonfinite << 21) |
+                           ((unsigned long long)ps.fallback << 42);
+  auto warp_fold = [&]() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+  };
+  warp_fold();
+  __syncthreads();  // the slots may still be read by an earlier reduction
+  if (l == 0) {
+    redd[w] = dsum;
+    redd[16 + w] = mx;
+    redi[w] = (int)(unsigned)cnt;
+    redi[16 + w] = (int)(unsigned)(cnt >> 32);
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const bool in = l < nw;
+    dsum = in ? redd[l] : 0.0;
+    mx = in ? redd[16 + l] : 0.0;
+    cnt = in ? ((unsigned long long)(unsigned)redi[l] | ((unsigned long long)(unsigned)redi[16 + l] << 32))
+             : 0ull;
+    warp_fold();
+  }
+  const int fl = (int)(cnt & 0x1FFFFFull);
+  const int nfin = (int)((cnt >> 21) & 0x1FFFFFull);
+  const int nfb = (int)(cnt >> 42);
   if (tid == 0) {
     atomicMax(&sp.st->maxdelta_bits, (unsigned long long)__double_as_longlong(mx));
     if (fl) atomicAdd(&sp.st->flips, (unsigned long long)fl);

@@ -120,3 +120,19 @@ __device__ __forceinline__ void bulk_wait_all() {
 }
 
 }  // namespace mbo
+
+namespace mbo {
+
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the kernel before it in the stream is still
+// running; pdl_wait() returns once that kernel has completed and its memory
+// operations are visible, so everything that reads its results (or the run
+// state it writes) comes after it.  pdl_release() lets the next such kernel
+// be scheduled as this grid's blocks retire.  Without the launch attribute
+// both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+}  // namespace mbo

@@ -25,6 +25,29 @@ inline __host__ __device__ constexpr int wcol_minb(int L, int TX) {
   return 512 / (TX * w_r(L) * w_lq(L)) > 0 ? 512 / (TX * w_r(L) * w_lq(L)) : 1;
 }
 
+// Whether the warp-plan launchers ask for programmatic dependent launch; the
+// host API sets it for each handle's launches (per host thread).
+bool& pdl_flag();
+
+// Launch with programmatic stream serialization (when pdl_flag()): the kernel
+// may be scheduled while the previous kernel of the stream finishes, and must
+// call pdl_wait() (mbo_tma.cuh) before it touches anything that kernel writes.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), int blocks, int threads, size_t smem,
+                              cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_flag() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 template <typename K> inline cudaError_t set_smem_once(K kernel, size_t bytes, size_t& done) {
   if (bytes <= 48 * 1024 || bytes <= done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

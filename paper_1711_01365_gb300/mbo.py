@@ -59,7 +59,7 @@ class MboError(RuntimeError):
 class mbo_config(C.Structure):
     _fields_ = [("fallback_sigma", C.c_double), ("check_interval", C.c_int), ("use_graph", C.c_int),
                 ("row_threads", C.c_int), ("axis_threads", C.c_int), ("axis_tx", C.c_int),
-                ("axis_stages", C.c_int), ("autotune", C.c_int)]
+                ("axis_stages", C.c_int), ("autotune", C.c_int), ("pdl", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

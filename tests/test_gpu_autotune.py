@@ -4,8 +4,9 @@ A tuned handle picks its strided-pass tile width, tile buffers, threads per
 block of the network passes and of the network row pass by timing candidate
 steps on a scratch field.  Launch shapes only decide which block computes
 which column or row: the arithmetic of every point is the same, so the field
-after a step must equal the default handle's bit for bit, and the FP64 energy
-may differ only by the order of its block sums.  A second handle of the same
+after a step must equal the default handle's bit for bit.  The energy may
+differ by the order of its partial sums: each thread accumulates its points in
+the field's precision (FP32 for the FP32 form) before the FP64 block sums.  A second handle of the same
 (dims, n, dtype) takes the cached choice.
 """
 import numpy as np
@@ -41,7 +42,7 @@ def test_tuned_step_equals_default_step(M, dims, n, dtype):
     assert ct["autotune"] == 1 and cd["autotune"] == 0
     nx = dims[-1]
     assert ct["axis_tx"] >= 1 and nx % ct["axis_tx"] == 0
-    assert ct["axis_stages"] in (1, 2)
+    assert ct["axis_stages"] in (1, 2) and ct["pdl"] in (1, 2)
     assert 64 <= ct["row_threads"] <= 384 and ct["row_threads"] % 32 == 0
     assert 64 <= ct["axis_threads"] <= 384 and ct["axis_threads"] % 32 == 0
     Ad, At = A0.clone(), A0.clone()
@@ -53,7 +54,8 @@ def test_tuned_step_equals_default_step(M, dims, n, dtype):
         assert torch.equal(Ad, At), f"step {k}: tuned launch shapes changed the field"
         assert rd["det_flips"] == rt["det_flips"]
         assert rd["fallback_points"] == rt["fallback_points"]
-        assert abs(rd["energy"] - rt["energy"]) <= 1e-12 * abs(rd["energy"])
+        etol = 1e-5 if dtype == "f32" else 1e-12
+        assert abs(rd["energy"] - rt["energy"]) <= etol * abs(rd["energy"])
     # the choice is cached for the process
     h2 = M.Mbo(dims, n, tau, dtype, autotune=1)
     assert M.mbo_launch_config(h2.h) == ct
@@ -101,3 +103,29 @@ def test_batch_with_autotune_equals_default_batch(M):
         assert torch.equal(a, b)
     bd.close()
     bt.close()
+
+
+@pytest.mark.parametrize("dims,n", [((1024, 1024), 3), ((2048, 256), 2), ((32, 64, 256), 3)])
+def test_dependent_launch_changes_nothing(M, dims, n):
+    """Programmatic dependent launch only moves when a pass is scheduled: the
+    fields, energies and statistics of a short run are those without it."""
+    tau = 3.0 / max(dims) ** 2
+    A0 = torch.tensor(O.project(I.gaussian(dims, n, 9), n), dtype=torch.float32, device="cuda")
+    out = []
+    for pdl in (1, 2):
+        h = M.Mbo(dims, n, tau, "f32", pdl=pdl)
+        assert M.mbo_launch_config(h.h)["pdl"] == pdl
+        A = A0.clone()
+        res = h.run(A, 12, -1.0)
+        torch.cuda.synchronize()
+        out.append((A, res))
+        h.close()
+    (A1, r1), (A2, r2) = out
+    assert torch.equal(A1, A2)
+    np.testing.assert_array_equal(r1["energies"], r2["energies"])
+    np.testing.assert_array_equal(r1["det_flips"], r2["det_flips"])
+
+
+def test_dependent_launch_option_checked(M):
+    with pytest.raises(M.MboError):
+        M.Mbo((64, 64), 2, 1e-3, "f32", pdl=3)
