@@ -42,7 +42,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   const long long P = g.P;
   const long long rows = P / N;
   const long long row0 = (long long)blockIdx.x * RB;
-  const bool live = row0 + row < rows;  // a whole sequence is live or not
+  const bool live = seq < RB * Q && row0 + row < rows;  // a whole sequence is live or not
   const long long off = (row0 + row) * N;
   float2* base = sm + seq * PS;  // this (row, plane)'s regions
   const float2* tw = static_cast<const float2*>(t.tw[0]);
@@ -149,7 +149,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   if constexpr (R > 1) __syncthreads();  // every group's transposes are done: the regions hold points now
 #pragma unroll
   for (int j = 0; j < E; ++j) base[R * (l + LQ * j) + r] = v[j];
-  float* fbM = reinterpret_cast<float*>(sm + RB * Q * PS);
+  float* fbM = reinterpret_cast<float*>(sm + wrow_nseq(N, NM) * PS);
   int* fbX = reinterpret_cast<int*>(fbM + kFallbackCap * C);
   if (tid == 0) s_nfb = 0;
   __syncthreads();
@@ -284,7 +284,9 @@ int warp_plan_radix(int N) { return w_r(N); }
 size_t wrow_smem_bytes(const Geom& g, int N, bool fallback) {
   const int LQ = w_lq(N), RB = wrow_rb(N), R = w_r(N);
   const size_t rs = (size_t)(LQ + 1) * (w_m(N) / LQ);
-  size_t b = (size_t)RB * g.Q * R * rs * sizeof(float2);
+  const int threads = (RB * g.Q * R * LQ + 31) / 32 * 32;
+  const int nseq = (threads + R * LQ - 1) / (R * LQ);  // wrow_nseq(N, g.n)
+  size_t b = (size_t)nseq * R * rs * sizeof(float2);
   if (fallback) b += (size_t)kFallbackCap * ((size_t)g.C * sizeof(float) + sizeof(int));
   return (b + 15) & ~(size_t)15;
 }

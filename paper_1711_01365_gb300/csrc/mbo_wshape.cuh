@@ -9,16 +9,33 @@ namespace mbo {
 inline __host__ __device__ constexpr int w_r(int N) { return N % 3 == 0 ? 3 : (N > 1024 ? 2 : 1); }
 inline __host__ __device__ constexpr int w_m(int N) { return N / w_r(N); }
 inline __host__ __device__ constexpr int w_lq(int N) { return w_m(N) == 1024 ? 32 : 16; }
-inline __host__ __device__ constexpr int wrow_rb(int N) { return w_lq(N) == 32 ? 1 : 2; }  // rows per block: whole warps
-inline __host__ __device__ constexpr int wrow_threads(int N, int NM) {
+// Rows per block of the x pass: one row where a sequence takes 32 lanes or
+// three 16-lane groups, else two rows (whole warps for any channel count).
+inline __host__ __device__ constexpr int wrow_rb(int N) {
+  return (w_lq(N) == 32 || w_r(N) == 3) ? 1 : 2;
+}
+// Lanes of the block's sequences (rows x complex planes x groups x lanes),
+// and threads: the lanes rounded up to whole warps.  The extra lanes (three
+// 16-lane groups, odd plane counts) form a partial sequence that runs the
+// warps' transposes on a shared-memory region of its own and stores nothing.
+inline __host__ __device__ constexpr int wrow_lanes(int N, int NM) {
   return wrow_rb(N) * ((NM * NM + 1) / 2) * w_r(N) * w_lq(N);
+}
+inline __host__ __device__ constexpr int wrow_threads(int N, int NM) {
+  return (wrow_lanes(N, NM) + 31) / 32 * 32;
+}
+// Sequences with a shared-memory region, the partial one included.
+inline __host__ __device__ constexpr int wrow_nseq(int N, int NM) {
+  return (wrow_threads(N, NM) + w_r(N) * w_lq(N) - 1) / (w_r(N) * w_lq(N));
 }
 
 // Blocks per SM the register budget is sized for: the x pass at 96 registers
-// (n <= 3) or 128 (n = 4), the strided passes at 128.
+// (n <= 3) or 128 (n = 4), the strided passes at 128.  Registers are
+// allocated per SM sub-partition (16384 each, warps spread over four), so at
+// B registers a thread an SM holds 4 * floor(16384 / (32 B)) warps.
 inline __host__ __device__ constexpr int wrow_minb(int N, int NM) {
-  return 65536 / (wrow_threads(N, NM) * (NM <= 3 ? 96 : 128)) > 0
-             ? 65536 / (wrow_threads(N, NM) * (NM <= 3 ? 96 : 128))
+  return (4 * (16384 / (32 * (NM <= 3 ? 96 : 128)))) / (wrow_threads(N, NM) / 32) > 0
+             ? (4 * (16384 / (32 * (NM <= 3 ? 96 : 128)))) / (wrow_threads(N, NM) / 32)
              : 1;
 }
 inline __host__ __device__ constexpr int wcol_minb(int L, int TX) {
