@@ -286,8 +286,17 @@ def bench_batched(args, torch, M):
     t = sum(a.elapsed_time(e) for a, e in ev) / 1e3
     pts = sum(int(np.prod(d)) for d in dims_l)
     b.close()
+    # minimal 2-D schedule of every field: two fused passes over its spectrum, 4 S_i
+    step_bytes = sum(4 * int(np.prod(d)) * n * n * 4 for d, n in zip(dims_l, n_l))
+    hbm, peak_kind = load_peaks()
+    ach = step_bytes / (t / K) / 1e9
     return {"value": pts * K / t, "unit": UNIT, "fields": len(spec), "points": pts, "steps": K,
             "ms_per_step": 1e3 * t / K, "dtype": "f32",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_kind": peak_kind, "traffic": None,
+                         "alg_bytes_per_step": step_bytes,
+                         "basis": "sum over the fields of 4 S_i (S_i = P_i n_i^2 4 B), the whole "
+                                  "batch step"},
             "note": "96 fields 256^2..2048^2, n=2/3, tau=4h^2, one graph launch per batch step, "
                     "working set > L2 (no flush)"}
 

@@ -84,7 +84,10 @@ typedef struct {
                             two dividing Nx, at most 16; 0 = automatic.           */
   int axis_stages;       /* MBO_F32 y / z passes of length 256..2048: tile
                             buffers per block, 1 or 2 (2: the next tile's copy is
-                            in flight while a tile is transformed); 0 = automatic. */
+                            in flight while a tile is transformed), or 3: one
+                            tile buffer and a separate transpose buffer (the
+                            next copy goes out once a tile is in registers);
+                            0 = automatic.                                      */
   int autotune;          /* 1: mbo_create times the candidate launch shapes of
                             this geometry (tile width, tile buffers, threads per
                             block of the strided and row passes, dependent

@@ -22,6 +22,9 @@ namespace {
 
 constexpr int kBoxRows = 256;  // TMA box extent along the transformed axis (the hardware limit)
 
+// Swizzle span of a tile (bytes): one tile row (TX * 8 bytes).
+constexpr int wcol_swizzle(int L, int TX) { return (void)L, TX * 8; }
+
 template <int L, int TX> struct WcolShape {
   static constexpr int R = w_r(L), M = w_m(L), LQ = w_lq(L);
   using F = WarpFFTR<M, LQ, R, TwShared>;
@@ -31,19 +34,26 @@ template <int L, int TX> struct WcolShape {
   static constexpr int TILE = L * TX;   // tile slots (float2), dense, swizzled by TMA
   static constexpr int BUF = (TILE > TX * PS ? TILE : TX * PS);
   static constexpr int BUF_BYTES = ((BUF * 8 + 1023) / 1024) * 1024;
+  // split staging (NBUF = 3): a tile buffer the copies use and a separate
+  // transpose / store buffer
+  static constexpr int TILE_BYTES = ((TILE * 8 + 1023) / 1024) * 1024;
+  static constexpr int SCR_BYTES = ((TX * PS * 8 + 1023) / 1024) * 1024;
   static constexpr int BOX = L < kBoxRows ? L : kBoxRows;
   static constexpr int NBOX = L / BOX;
-  // 16-byte chunk swizzle of the TMA tile: span TX * 8 bytes (32, 64 or 128)
-  static constexpr int SWM = TX * 8 / 16 - 1;
+  // 16-byte chunk swizzle of the TMA tile, span SWB bytes (wcol_swizzle)
+  static constexpr int SWB = wcol_swizzle(L, TX);
+  static constexpr int SWM = SWB / 16 - 1;
   static_assert(TX == 4 || TX == 8 || TX == 16, "tile widths 4, 8, 16");
-  static_assert((R * LQ) % 8 == 0, "the lane's swizzle term must not depend on j");
+  static_assert((R * LQ * TX) % SWB == 0, "the lane's swizzle term must not depend on j");
 };
 
-// Shared-memory bytes: NBUF tile buffers, the axis twiddles (L complex) and
-// the axis multiplier and 1 - g (L reals each), plus 1 KB of alignment slack.
+// Shared-memory bytes: NBUF tile buffers (NBUF = 3: one tile buffer and one
+// transpose buffer), the axis twiddles (L complex) and the axis multiplier and
+// 1 - g (L reals each), plus 1 KB of alignment slack.
 template <int L, int TX> constexpr size_t wcol_smem(int nbuf) {
   using S = WcolShape<L, TX>;
-  return 1024 + (size_t)nbuf * S::BUF_BYTES + (size_t)L * 8 + (size_t)L * 8;
+  const size_t bufs = nbuf == 3 ? (size_t)S::TILE_BYTES + S::SCR_BYTES : (size_t)nbuf * S::BUF_BYTES;
+  return 1024 + bufs + (size_t)L * 8 + (size_t)L * 8;
 }
 
 template <int MODE, int L, int TX, int NBUF>
@@ -53,16 +63,21 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
   using S = WcolShape<L, TX>;
   using F = typename S::F;
   constexpr int R = S::R, M = S::M, LQ = S::LQ, E = S::E, NT = S::NT, PS = S::PS;
+  // NBUF = 3: the next tile's copy goes out as soon as a tile is in registers,
+  // into the one tile buffer; transposes and the store use a buffer of their own
+  constexpr bool SPLIT = NBUF == 3;
+  constexpr int NBAR = SPLIT ? 1 : NBUF;  // tile buffers the copies land in
   extern __shared__ unsigned char smem_raw[];
   __shared__ double redd[32];
   __shared__ int s_flag;
-  __shared__ __align__(8) unsigned long long bar[NBUF];
+  __shared__ __align__(8) unsigned long long bar[NBAR];
 
   // 1024-byte aligned tile buffers (the TMA swizzle works on address bits
   // 4..9); offsetting the shared array itself keeps every access below a
   // shared-memory instruction
   unsigned char* al = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  float2* s_tw = reinterpret_cast<float2*>(al + NBUF * S::BUF_BYTES);
+  float2* s_tw = reinterpret_cast<float2*>(al + (SPLIT ? S::TILE_BYTES + S::SCR_BYTES : NBUF * S::BUF_BYTES));
+  float2* scr = reinterpret_cast<float2*>(al + S::TILE_BYTES);  // SPLIT: transposes, store
   float* s_g = reinterpret_cast<float*>(s_tw + L);
   float* s_om = s_g + L;
 
@@ -97,7 +112,7 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
 
   if (tid == 0) {
 #pragma unroll
-    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+    for (int b = 0; b < NBAR; ++b) mbar_init(&bar[b], 1);
     fence_barrier_init();
   }
   {  // the tables are the handle's own: staged while the previous pass finishes
@@ -114,9 +129,9 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
   if (sp.respect_stop && *(volatile int*)&sp.st->stop) return;
   pdl_release();
   if (tid == 0) {
-    for (int k = 0; k < NBUF && blockIdx.x + k * gridDim.x < ntiles; ++k)
+    for (int k = 0; k < NBAR && blockIdx.x + k * gridDim.x < ntiles; ++k)
       issue_load(blockIdx.x + k * gridDim.x, k);
-    if (blockIdx.x + NBUF * gridDim.x < ntiles) prefetch_tile(blockIdx.x + NBUF * gridDim.x);
+    if (blockIdx.x + NBAR * gridDim.x < ntiles) prefetch_tile(blockIdx.x + NBAR * gridDim.x);
     // the caller's L2 hint: this block's share of a buffer the next pass reads
     if (pf_bytes > 0) {
       const long long chunk = ((pf_bytes / gridDim.x + 4095) / 4096) * 4096;
@@ -131,17 +146,17 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
   __syncthreads();
 
   // the lane's rows are R (l + LQ j) + r; their swizzle term depends on l and r only
+  // (TMA swizzle: the 16-byte chunk bits 4..6 of an offset XOR its bits 7..9)
   const int xr = ((((R * l + r) * TX * 8) >> 7) & S::SWM);
-  const int cs = c ^ (xr << 1);
-  const int lane_slot = (R * l + r) * TX + cs;
+  const int lane_slot = ((R * l + r) * TX + c) ^ (xr << 1);
   constexpr int JSTRIDE = R * LQ * TX;
 
   float acc = 0.f;
   bool ok = true;
   int it = 0;
   for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++it) {
-    const int buf = NBUF == 1 ? 0 : (it & 1);
-    const unsigned parity = NBUF == 1 ? (it & 1) : ((it >> 1) & 1);
+    const int buf = NBAR == 1 ? 0 : (it & 1);
+    const unsigned parity = NBAR == 1 ? (it & 1) : ((it >> 1) & 1);
     float2* tile = reinterpret_cast<float2*>(al + buf * S::BUF_BYTES);
     // this tile's per-column factors, loaded before the wait so that their
     // latency overlaps it: g_x, 1 - g_x and the Parseval weight of column x
@@ -161,12 +176,22 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
     }
     ok = __syncthreads_and(mbar_wait_bounded(&bar[buf], parity)) != 0;
     if (!ok) break;
-    if (tid == 0 && it > 0 && b + NBUF * gridDim.x < ntiles) prefetch_tile(b + NBUF * gridDim.x);
+    // L2 prefetch of the tile loaded one copy later (SPLIT: the prologue
+    // covered b + gridDim.x, loaded below)
+    if (SPLIT) {
+      if (tid == 0 && b + 2 * gridDim.x < ntiles) prefetch_tile(b + 2 * gridDim.x);
+    } else if (tid == 0 && it > 0 && b + NBAR * gridDim.x < ntiles) {
+      prefetch_tile(b + NBAR * gridDim.x);
+    }
     float2 v[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = tile[lane_slot + j * JSTRIDE];
-    __syncthreads();  // the tile is in registers: its buffer holds the transposes now
-    float2* cbase = tile + c * PS;
+    // SPLIT: the previous tile's store has read the transpose buffer
+    if (SPLIT && tid == 0) bulk_wait_read_all();
+    __syncthreads();  // the tile is in registers: its buffer is free (holds the transposes)
+    if (SPLIT && tid == 0 && b + gridDim.x < ntiles) issue_load(b + gridDim.x, 0);
+    float2* work = SPLIT ? scr : tile;  // transposes and the store
+    float2* cbase = work + c * PS;
     const float2* tw = s_tw;
     const float2* twr = s_tw + M;
     if (MODE != AXIS_INV) F::fwd(v, cbase, r, tw, twr, l);
@@ -190,25 +215,25 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
     }
     if (MODE == AXIS_FGI || MODE == AXIS_INV) F::inv(v, cbase, r, tw, twr, l);
     __syncthreads();  // every column's transposes are done
-    const int nb = b + NBUF * gridDim.x;  // the tile that reuses this buffer
+    const int nb = b + NBAR * gridDim.x;  // the tile that reuses this buffer (not SPLIT)
     if (MODE != AXIS_ENERGY) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) tile[lane_slot + j * JSTRIDE] = v[j];
+      for (int j = 0; j < E; ++j) work[lane_slot + j * JSTRIDE] = v[j];
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
 #pragma unroll
         for (int bx = 0; bx < S::NBOX; ++bx) {
-          if (axis == 1) tma_store_4d(&tm, x0, bx * S::BOX, o, q, tile + bx * S::BOX * TX);
-          else tma_store_4d(&tm, x0, o, bx * S::BOX, q, tile + bx * S::BOX * TX);
+          if (axis == 1) tma_store_4d(&tm, x0, bx * S::BOX, o, q, work + bx * S::BOX * TX);
+          else tma_store_4d(&tm, x0, o, bx * S::BOX, q, work + bx * S::BOX * TX);
         }
         bulk_commit();
-        if (nb < ntiles) {
+        if (!SPLIT && nb < ntiles) {
           bulk_wait_read_all();  // the store has read the buffer: the next load may overwrite it
           issue_load(nb, buf);
         }
       }
-    } else if (tid == 0 && nb < ntiles) {
+    } else if (!SPLIT && tid == 0 && nb < ntiles) {
       issue_load(nb, buf);
     }
   }
@@ -218,7 +243,7 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
     // flight a bounded wait, and leave (statistics of this launch are void)
     if (tid == 0) {
       atomicOr(&sp.st->err, kErrWaitTimeout);
-      for (int k = 0; k < NBUF; ++k) (void)mbar_wait_bounded(&bar[k], 0), (void)mbar_wait_bounded(&bar[k], 1);
+      for (int k = 0; k < NBAR; ++k) (void)mbar_wait_bounded(&bar[k], 0), (void)mbar_wait_bounded(&bar[k], 1);
     }
     return;
   }
@@ -295,6 +320,7 @@ template <int L, int TX>
 cudaError_t wcol_ltx(AxisMode mode, int axis, const Geom& g, const Tables<float>& t,
                      const CUtensorMap* tm, const StatsPtrs& sp, cudaStream_t s, bool prep,
                      int stages, L2Hint pf) {
+  if (stages == 3) return wcol_ltxb<L, TX, 3>(mode, axis, g, t, tm, sp, s, prep, pf);
   if (stages == 2) return wcol_ltxb<L, TX, 2>(mode, axis, g, t, tm, sp, s, prep, pf);
   return wcol_ltxb<L, TX, 1>(mode, axis, g, t, tm, sp, s, prep, pf);
 }
@@ -341,9 +367,10 @@ bool wcol_tensor_map(CUtensorMap* map, void* W, const Geom& g, int axis, int tx)
   const cuuint32_t bx = (cuuint32_t)(L < kBoxRows ? L : kBoxRows);
   const cuuint32_t box[4] = {(cuuint32_t)tx, axis == 1 ? bx : 1u, axis == 1 ? 1u : bx, 1u};
   const cuuint32_t es[4] = {1, 1, 1, 1};
-  const CUtensorMapSwizzle sw = tx * 8 == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
-                                : tx * 8 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                               : CU_TENSOR_MAP_SWIZZLE_32B;
+  const int swb = wcol_swizzle(L, tx);
+  const CUtensorMapSwizzle sw = swb == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                            : CU_TENSOR_MAP_SWIZZLE_32B;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

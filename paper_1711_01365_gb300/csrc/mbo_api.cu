@@ -542,7 +542,7 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   for (int t : {h->tx, h->tx / 2, 4})
     if (t >= 1 && std::find(txs.begin(), txs.end(), t) == txs.end()) txs.push_back(t);
   if (c.axis_tx) txs = {h->tx};
-  stages = (warp_axis && !c.axis_stages) ? std::vector<int>{1, 2} : std::vector<int>{h->axis_stages};
+  stages = (warp_axis && !c.axis_stages) ? std::vector<int>{1, 2, 3} : std::vector<int>{h->axis_stages};
   athreads = (net_axis && !c.axis_threads) ? std::vector<int>{128, 256, 384}
                                            : std::vector<int>{h->axis_threads};
   rthreads = (net_row && !c.row_threads) ? std::vector<int>{64, 128, 192, 256, 384}
@@ -721,7 +721,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
     h->tx = c.axis_tx;
   }
   if (c.axis_stages) {
-    if (c.axis_stages < 1 || c.axis_stages > 2) {
+    if (c.axis_stages < 1 || c.axis_stages > 3) {
       delete h;
       return MBO_ERR_INVALID_ARG;
     }

@@ -42,7 +42,7 @@ def test_tuned_step_equals_default_step(M, dims, n, dtype):
     assert ct["autotune"] == 1 and cd["autotune"] == 0
     nx = dims[-1]
     assert ct["axis_tx"] >= 1 and nx % ct["axis_tx"] == 0
-    assert ct["axis_stages"] in (1, 2) and ct["pdl"] in (1, 2)
+    assert ct["axis_stages"] in (1, 2, 3) and ct["pdl"] in (1, 2)
     assert 64 <= ct["row_threads"] <= 384 and ct["row_threads"] % 32 == 0
     assert 64 <= ct["axis_threads"] <= 384 and ct["axis_threads"] % 32 == 0
     Ad, At = A0.clone(), A0.clone()
@@ -129,3 +129,28 @@ def test_dependent_launch_changes_nothing(M, dims, n):
 def test_dependent_launch_option_checked(M):
     with pytest.raises(M.MboError):
         M.Mbo((64, 64), 2, 1e-3, "f32", pdl=3)
+
+
+@pytest.mark.parametrize("dims", [(256, 64), (512, 64), (768, 64), (1024, 64), (1536, 64),
+                                  (2048, 64), (512, 16, 64)])
+def test_strided_pass_shapes_change_nothing(M, dims):
+    """Every tile width and staging form of the FP32 strided passes gives the
+    field of the default launch bit for bit (two steps, n = 3)."""
+    n = 3
+    tau = 3.0 / max(dims) ** 2
+    A0 = torch.tensor(O.project(I.gaussian(dims, n, 13), n), dtype=torch.float32, device="cuda")
+    ref = None
+    for tx in (8, 4):
+        for stages in (1, 2, 3):
+            h = M.Mbo(dims, n, tau, "f32", axis_tx=tx, axis_stages=stages)
+            A = A0.clone()
+            r1 = h.step(A, want_stats=True)
+            r2 = h.step(A, flags=M.MBO_STEP_CONTINUE, want_stats=True)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = (A, r1, r2)
+            else:
+                assert torch.equal(A, ref[0]), (tx, stages)
+                assert r2["det_flips"] == ref[2]["det_flips"]
+                assert abs(r2["energy"] - ref[2]["energy"]) <= 1e-5 * abs(ref[2]["energy"])
+            h.close()
