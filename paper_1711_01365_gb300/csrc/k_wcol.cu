@@ -328,13 +328,18 @@ cudaError_t wcol_ltx(AxisMode mode, int axis, const Geom& g, const Tables<float>
 }  // namespace
 
 int warp_tile(int L, int nx, int tx) {
-  const int t = (tx >= 8 && L <= 1024) ? 8 : 4;  // 1536 and 2048: 4 columns (tile size)
+  // 16 columns (one 128-byte line per tile row) up to 512 rows; 1536 and 2048:
+  // 4 columns (tile size)
+  if (tx >= 16 && L <= 512 && nx % 16 == 0) return 16;
+  const int t = (tx >= 8 && L <= 1024) ? 8 : 4;
   return (nx % t == 0) ? t : 0;
 }
 
 size_t wcol_smem_bytes(int L, int tx, int stages) {
 #define MBO_WSM(LEN)                                        \
   if (L == LEN) return tx == 8 ? wcol_smem<LEN, 8>(stages) : wcol_smem<LEN, 4>(stages);
+  if (L == 256 && tx == 16) return wcol_smem<256, 16>(stages);
+  if (L == 512 && tx == 16) return wcol_smem<512, 16>(stages);
   MBO_WSM(256)
   MBO_WSM(512)
   MBO_WSM(768)
@@ -389,6 +394,10 @@ cudaError_t launch_wcol(AxisMode mode, int axis, const Geom& g, const Tables<flo
     if (TX == 8) return wcol_ltx<LEN, 8>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf); \
     if (TX == 4) return wcol_ltx<LEN, 4>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf); \
   }
+  if (L == 512 && TX == 16)
+    return wcol_ltx<512, 16>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf);
+  if (L == 256 && TX == 16)
+    return wcol_ltx<256, 16>(mode, axis, g, t, tm, sp, s, prepare_only, stages, pf);
   MBO_WCOL_CASE(1024)
   MBO_WCOL_CASE(512)
   MBO_WCOL_CASE(256)

@@ -460,13 +460,13 @@ template <typename R> __global__ void k_tune_fill(R* A, long long n) {
 bool shape_fits(mbo_ctx* h, const LaunchShape& c, int maxsm) {
   const Geom& g = h->g;
   if (c.tx < 1 || g.nx % c.tx) return false;
-  if (axis_smem_bytes(std::max(g.ny, g.nz), c.tx, h->elem) > (size_t)maxsm) return false;
-  if (h->dtype == MBO_F32) {
-    for (int ax = 1; ax < g.ndim; ++ax) {
-      if (!h->tf.plan[ax].lq) continue;
-      const int L = ax == 1 ? g.ny : g.nz;
+  for (int ax = 1; ax < g.ndim; ++ax) {
+    const int L = ax == 1 ? g.ny : g.nz;
+    if (h->dtype == MBO_F32 && h->tf.plan[ax].lq) {
       const int wt = warp_tile(L, g.nx, c.tx);
       if (!wt || wcol_smem_bytes(L, wt, c.stages) > (size_t)maxsm) return false;
+    } else if (axis_smem_bytes(L, c.tx, h->elem) > (size_t)maxsm) {
+      return false;
     }
   }
   return true;
@@ -539,8 +539,8 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   }
   const bool net_row = !(f32 && h->tf.plan[0].lq);
   std::vector<int> txs, stages, athreads, rthreads;
-  for (int t : {h->tx, h->tx / 2, 4})
-    if (t >= 1 && std::find(txs.begin(), txs.end(), t) == txs.end()) txs.push_back(t);
+  for (int t : {h->tx, 2 * h->tx, h->tx / 2, 4})
+    if (t >= 1 && t <= 16 && std::find(txs.begin(), txs.end(), t) == txs.end()) txs.push_back(t);
   if (c.axis_tx) txs = {h->tx};
   stages = (warp_axis && !c.axis_stages) ? std::vector<int>{1, 2, 3} : std::vector<int>{h->axis_stages};
   athreads = (net_axis && !c.axis_threads) ? std::vector<int>{128, 256, 384}
@@ -705,6 +705,17 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
                    : g.nx >= 1024 ? (dtype == MBO_F32 ? 192 : 128)
                    : (g.nx >= 256 ? 128 : (g.nx >= 64 ? 64 : 32));
   h->axis_threads = 256;
+  if (dtype == MBO_F32) {
+    // FP32 warp-plan strided passes, measured on GB300: 16-column tiles (one
+    // 128-byte line per tile row) where an axis of 512 is strided (512^3:
+    // 13.7 -> 10.4 ms per step; 512^2, n = 2: 32 -> 26 us), and split staging
+    // with them and in 3-D (512^3: 10.4 -> 9.9 ms; 256^3: 1.36 -> 1.28 ms)
+    bool l512 = false;
+    for (int ax = 1; ax < ndim; ++ax)
+      l512 = l512 || ((ax == 1 ? g.ny : g.nz) == 512 && axis_plan(g, ax, true).lq);
+    if (l512 && g.nx % 16 == 0) h->tx = 16;
+    if (h->tx == 16 || ndim == 3) h->axis_stages = 3;
+  }
   const mbo_config& c = h->cfg;
   if (c.row_threads) {
     if (c.row_threads < 32 || c.row_threads > kMaxThreads || c.row_threads % 32) {
@@ -743,16 +754,17 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   if (dtype == MBO_F32 && axis_plan(g, 0, true).lq)
     h->pdl = c.pdl == 1 || (c.pdl == 0 && wrow_waves(g) <= 2.0);
   size_t rs = row_smem_bytes(g, h->elem, true);
-  size_t as = axis_smem_bytes(std::max(g.ny, g.nz), h->tx, h->elem);
+  size_t as = 0;       // shared memory of the strided passes, each by its own plan
   int min_tx = h->tx;  // narrowest column tile of any strided pass
-  if (dtype == MBO_F32) {
-    if (axis_plan(g, 0, true).lq) rs = std::max(rs, wrow_smem_bytes(g, g.nx, true));
-    for (int ax = 1; ax < ndim; ++ax) {
-      const int L = ax == 1 ? g.ny : g.nz;
-      if (!axis_plan(g, ax, true).lq) continue;
+  if (dtype == MBO_F32 && axis_plan(g, 0, true).lq) rs = std::max(rs, wrow_smem_bytes(g, g.nx, true));
+  for (int ax = 1; ax < ndim; ++ax) {
+    const int L = ax == 1 ? g.ny : g.nz;
+    if (dtype == MBO_F32 && axis_plan(g, ax, true).lq) {
       const int wt = warp_tile(L, g.nx, h->tx);
       as = std::max(as, wcol_smem_bytes(L, wt, h->axis_stages));
       min_tx = std::min(min_tx, wt);
+    } else {
+      as = std::max(as, axis_smem_bytes(L, h->tx, h->elem));
     }
   }
   int maxsm = 0;
@@ -808,6 +820,7 @@ mbo_status mbo_create(mbo_handle* out, int ndim, const int64_t* dims, int n, dou
   const cudaError_t pe = dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx, h->axis_stages)
                                           : prepare_kernels<double>(g, h->td, h->tx, 1);
   if (pe != cudaSuccess) {
+    (void)cudaGetLastError();  // the failed attribute call must not surface at a later launch
     mbo_destroy(h);
     return MBO_ERR_CUDA;
   }

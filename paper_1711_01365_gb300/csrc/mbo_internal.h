@@ -214,7 +214,7 @@ bool& pdl_flag();  // programmatic dependent launch of these passes (per host th
 double wrow_waves(const Geom& g);  // waves of blocks of the projecting x pass
 bool warp_plan_length(int N);
 int warp_plan_radix(int N);
-int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4 or 8; 0: none)
+int warp_tile(int L, int nx, int tx);  // columns per tile of the strided pass (4, 8 or 16; 0: none)
 size_t wrow_smem_bytes(const Geom& g, int N, bool fallback);
 size_t wcol_smem_bytes(int L, int tx, int stages);
 cudaError_t launch_wrow(RowMode mode, const Geom& g, const Tables<float>& t, const float* A_in,

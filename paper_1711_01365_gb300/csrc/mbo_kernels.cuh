@@ -782,6 +782,7 @@ template <typename R> cudaError_t prepare_kernels(const Geom& g, const Tables<R>
   MBO_PREP_ROW(4)
 #undef MBO_PREP_ROW
   for (int axis = 1; axis <= (g.ndim == 3 ? 2 : 1) && e == cudaSuccess; ++axis) {
+    if (sizeof(R) == 4 && tabs.plan[axis].lq) continue;  // the warp-plan pass above takes this axis
     e = launch_axis_m<R, AXIS_FWD>(g, t, nullptr, sp, axis, tx, 64, 0, true);
     if (e == cudaSuccess) e = launch_axis_m<R, AXIS_INV>(g, t, nullptr, sp, axis, tx, 64, 0, true);
     if (e == cudaSuccess) e = launch_axis_m<R, AXIS_FGI>(g, t, nullptr, sp, axis, tx, 64, 0, true);

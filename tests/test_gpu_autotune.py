@@ -43,7 +43,7 @@ def test_tuned_step_equals_default_step(M, dims, n, dtype):
     nx = dims[-1]
     assert ct["axis_tx"] >= 1 and nx % ct["axis_tx"] == 0
     assert ct["axis_stages"] in (1, 2, 3) and ct["pdl"] in (1, 2)
-    assert 64 <= ct["row_threads"] <= 384 and ct["row_threads"] % 32 == 0
+    assert 32 <= ct["row_threads"] <= 384 and ct["row_threads"] % 32 == 0
     assert 64 <= ct["axis_threads"] <= 384 and ct["axis_threads"] % 32 == 0
     Ad, At = A0.clone(), A0.clone()
     for k in range(3):
@@ -134,13 +134,13 @@ def test_dependent_launch_option_checked(M):
 @pytest.mark.parametrize("dims", [(256, 64), (512, 64), (768, 64), (1024, 64), (1536, 64),
                                   (2048, 64), (512, 16, 64)])
 def test_strided_pass_shapes_change_nothing(M, dims):
-    """Every tile width and staging form of the FP32 strided passes gives the
+    """Every tile width (16 columns up to 512 rows) and staging form of the FP32 strided passes gives the
     field of the default launch bit for bit (two steps, n = 3)."""
     n = 3
     tau = 3.0 / max(dims) ** 2
     A0 = torch.tensor(O.project(I.gaussian(dims, n, 13), n), dtype=torch.float32, device="cuda")
     ref = None
-    for tx in (8, 4):
+    for tx in (8, 16, 4):
         for stages in (1, 2, 3):
             h = M.Mbo(dims, n, tau, "f32", axis_tx=tx, axis_stages=stages)
             A = A0.clone()
