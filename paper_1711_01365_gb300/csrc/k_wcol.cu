@@ -12,6 +12,8 @@
 //           transform, all in registers; the result goes back by TMA store.
 //           With NBUF = 2 the next tile's load is in flight while a tile is
 //           transformed.
+#include <type_traits>
+
 #include "mbo_kernels.cuh"
 #include "mbo_tma.cuh"
 #include "mbo_wfft.cuh"
@@ -27,7 +29,11 @@ constexpr int wcol_swizzle(int L, int TX) { return (void)L, TX * 8; }
 
 template <int L, int TX> struct WcolShape {
   static constexpr int R = w_r(L), M = w_m(L), LQ = w_lq(L);
-  using F = WarpFFTR<M, LQ, R, TwShared>;
+  // 2048 = 2 x 1024: the cross-group stage first, so that a warp reads
+  // consecutive tile rows (8 of 16 bank pairs per access instead of 4)
+  static constexpr bool DIF = R == 2;
+  using F = typename std::conditional<DIF, WarpFFTRdif<M, LQ, R, TwShared>,
+                                      WarpFFTR<M, LQ, R, TwShared>>::type;
   static constexpr int E = F::E;
   static constexpr int NT = TX * R * LQ;
   static constexpr int PS = R * F::RS;  // transpose slots of one column (padded rows)
@@ -44,7 +50,8 @@ template <int L, int TX> struct WcolShape {
   static constexpr int SWB = wcol_swizzle(L, TX);
   static constexpr int SWM = SWB / 16 - 1;
   static_assert(TX == 4 || TX == 8 || TX == 16, "tile widths 4, 8, 16");
-  static_assert((R * LQ * TX) % SWB == 0, "the lane's swizzle term must not depend on j");
+  static_assert(((DIF ? 1 : R) * LQ * TX) % SWB == 0 && (M * TX) % SWB == 0,
+                "the lane's swizzle term must not depend on j or r");
 };
 
 // Shared-memory bytes: NBUF tile buffers (NBUF = 3: one tile buffer and one
@@ -147,9 +154,11 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
 
   // the lane's rows are R (l + LQ j) + r; their swizzle term depends on l and r only
   // (TMA swizzle: the 16-byte chunk bits 4..6 of an offset XOR its bits 7..9)
-  const int xr = ((((R * l + r) * TX * 8) >> 7) & S::SWM);
-  const int lane_slot = ((R * l + r) * TX + c) ^ (xr << 1);
-  constexpr int JSTRIDE = R * LQ * TX;
+  // rows: R (l + LQ j) + r, or with the cross-group stage first l + LQ j + M r
+  const int row0 = S::DIF ? l + M * r : R * l + r;
+  const int xr = (((row0 * TX * 8) >> 7) & S::SWM);
+  const int lane_slot = (row0 * TX + c) ^ (xr << 1);
+  constexpr int JSTRIDE = (S::DIF ? 1 : R) * LQ * TX;
 
   float acc = 0.f;
   bool ok = true;
@@ -203,7 +212,8 @@ k_wcol(Geom g, Tables<float> t, const __grid_constant__ CUtensorMap tm, StatsPtr
       const float omb = omx + gxx * omo;
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const int p = l + LQ * j + M * r;  // group r holds frequencies k' + M r
+        // group r holds frequencies k' + M r, or R k' + r (k' = l + LQ j)
+        const int p = S::DIF ? R * (l + LQ * j) + r : l + LQ * j + M * r;
         const float omv = omb + omo2 * s_om[p];  // 1 - g without cancellation
         const float2 z = v[j];
         acc += wx * omv * (z.x * z.x + z.y * z.y);

@@ -225,4 +225,75 @@ template <int M, int LQ, int R, class TW = TwGlobal> struct WarpFFTR {
   }
 };
 
+// The same lengths with the cross-group stage first (decimation in frequency
+// across the groups): group r holds the contiguous sub-sequence a[x' + M r]
+// (x' = l + LQ j); a length-R DFT across the groups and the twiddle W_N^(x' s)
+// precede the length-M transform, after which group s holds X[R k' + s] at
+// k' = l + LQ j:
+//   X[R k' + s] = sum_x' W_M^(x' k') W_N^(x' s) sum_r W_R^(r s) a[x' + M r].
+// The spectrum is decimated across the groups, so this form serves passes that
+// transform, multiply and transform back in registers (the strided passes):
+// lanes of a group read consecutive rows of a tile.  The inverse runs the steps
+// transposed and conjugated, in reverse (unnormalised).
+template <int M, int LQ, int R, class TW = TwGlobal> struct WarpFFTRdif {
+  using F = WarpFFT<M, LQ, TW>;
+  using D = WarpFFTR<M, LQ, R, TW>;  // rot()
+  static constexpr int E = F::E;
+  static constexpr int RS = F::RS;
+
+  // twr: W_N^(s x') at [(s - 1) * M + x']
+  template <typename V>
+  __device__ __forceinline__ static void fwd(V (&v)[E], V* base, int r, const V* __restrict__ tw,
+                                             const V* __restrict__ twr, int l) {
+    if constexpr (R == 1) {
+      F::fwd(v, base, tw, l);
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) base[r * RS + l + LQ * j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {  // this group now plays s = r
+      V acc = base[l + LQ * j];
+#pragma unroll
+      for (int rr = 1; rr < R; ++rr) acc = cadd(acc, D::rot(base[rr * RS + l + LQ * j], rr * r));
+      if (r > 0) acc = cmul(acc, TW::ld(&twr[(r - 1) * M + l + LQ * j]));
+      v[j] = acc;
+    }
+    __syncthreads();
+    F::fwd(v, base + r * RS, tw, l);
+  }
+
+  // group s holds X[R k' + s]  ->  group r holds sum_k X[k] exp(+2 pi i (x' + M r) k / N)
+  template <typename V>
+  __device__ __forceinline__ static void inv(V (&v)[E], V* base, int r, const V* __restrict__ tw,
+                                             const V* __restrict__ twr, int l) {
+    if constexpr (R == 1) {
+      F::inv(v, base, tw, l);
+      return;
+    }
+    F::inv(v, base + r * RS, tw, l);  // this group plays s = r
+    if (r > 0) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        V c = TW::ld(&twr[(r - 1) * M + l + LQ * j]);
+        c.y = -c.y;
+        v[j] = cmul(v[j], c);
+      }
+    }
+    // each group's region held only its own transposes: no barrier before
+#pragma unroll
+    for (int j = 0; j < E; ++j) base[r * RS + l + LQ * j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      V acc = base[l + LQ * j];
+#pragma unroll
+      for (int ss = 1; ss < R; ++ss) acc = cadd(acc, D::rot(base[ss * RS + l + LQ * j], (R - 1) * ss * r));
+      v[j] = acc;
+    }
+    __syncthreads();
+  }
+};
+
 }  // namespace mbo
