@@ -298,8 +298,13 @@ template <int NM, int N> double wrow_waves_nm(const Geom& g) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = wrow_smem_bytes(g, N, true);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, wrow_threads(N, NM), smem);
+  // a shape that does not fit is rejected by the caller; leave no error behind
+  if ((smem > 48 * 1024 &&
+       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, wrow_threads(N, NM), smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 1e9;
+  }
   const double blocks = (double)((g.P / N + wrow_rb(N) - 1) / wrow_rb(N));
   return blocks / ((double)sms * (per_sm > 0 ? per_sm : 1));
 }

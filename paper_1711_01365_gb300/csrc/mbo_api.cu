@@ -597,7 +597,10 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
             ? cudaSuccess
             : cudaErrorUnknown;
   h->w_valid_for = nullptr;
-  if (e != cudaSuccess) return MBO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();  // no stale error for the caller's next launch
+    return MBO_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best;
   return MBO_OK;
