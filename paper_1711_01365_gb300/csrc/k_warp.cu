@@ -21,7 +21,7 @@ namespace {
 template <int NM, int MODE, int N>
 __global__ void __launch_bounds__(wrow_threads(N, NM), wrow_minb(N, NM))
 k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2* W, StatsPtrs sp,
-       float fb_sigma, int ahead) {
+       float fb_sigma, int ahead, int persistent) {
   constexpr int R = w_r(N), M = w_m(N), LQ = w_lq(N), RB = wrow_rb(N);
   using F = WarpFFTR<M, LQ, R>;
   constexpr int C = NM * NM, Q = (C + 1) / 2, E = F::E, RS = F::RS, NT = wrow_threads(N, NM);
@@ -41,193 +41,204 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   const int row = seq / Q, q = seq - row * Q;
   const long long P = g.P;
   const long long rows = P / N;
-  const long long row0 = (long long)blockIdx.x * RB;
-  const bool live = seq < RB * Q && row0 + row < rows;  // a whole sequence is live or not
-  const long long off = (row0 + row) * N;
+  const long long ngroups = (rows + RB - 1) / RB;  // row groups: RB rows each
   float2* base = sm + seq * PS;  // this (row, plane)'s regions
   const float2* tw = static_cast<const float2*>(t.tw[0]);
   const float2* twr = tw + M;
+  float* fbM = reinterpret_cast<float*>(sm + wrow_nseq(N, NM) * PS);
+  int* fbX = reinterpret_cast<int*>(fbM + kFallbackCap * C);
+  const bool mirror = q == Q - 1 && g.xh < N;
   float2 v[E];
-  // the forward spectrum of this sequence to W; the last plane of an odd
-  // channel count is Hermitian: columns k < xh only
-  auto store_spectrum = [&](const float2(&u)[E]) {
-    if (!live) return;
-    float2* wdst = W + q * P + off;
-    if (q < Q - 1 || g.xh == N) {
+  PointStats<float> ps;  // projection mode: over all of the block's rows
+  double defect = 0.0;   // forward mode
+
+  // Row groups of this block: its own index, or with `persistent` the groups
+  // blockIdx.x, blockIdx.x + gridDim.x, ... (a grid of one wave).
+  const long long gstep = persistent ? gridDim.x : ngroups;
+  for (long long gi = blockIdx.x; gi < ngroups; gi += gstep) {
+    const long long row0 = gi * RB;
+    const bool live = seq < RB * Q && row0 + row < rows;  // a whole sequence is live or not
+    const long long off = (row0 + row) * N;
+    // the forward spectrum of this sequence to W; the last plane of an odd
+    // channel count is Hermitian: columns k < xh only
+    auto store_spectrum = [&](const float2(&u)[E]) {
+      if (!live) return;
+      float2* wdst = W + q * P + off;
+      if (q < Q - 1 || g.xh == N) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) wdst[l + M * r + LQ * j] = u[j];
+        for (int j = 0; j < E; ++j) wdst[l + M * r + LQ * j] = u[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int k = l + LQ * j + M * r;
+          if (k < g.xh) wdst[k] = u[j];
+        }
+      }
+    };
+    if (gi != blockIdx.x) __syncthreads();  // the previous group's regions are free
+
+    if (MODE == ROW_FWD) {
+      // per point: load all channels, accumulate n - |A|^2, park the planes
+      for (int p = tid; p < RB * N; p += NT) {
+        const int rw = p / N, x = p - rw * N;
+        if (row0 + rw >= rows) continue;
+        const long long o = (row0 + rw) * N + x;
+        float sq = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) {
+          const float re = Ain[(2 * qq) * P + o];
+          const float im = (2 * qq + 1 < C) ? Ain[(2 * qq + 1) * P + o] : 0.f;
+          sm[(rw * Q + qq) * PS + x] = float2{re, im};
+          sq += re * re + im * im;
+        }
+        defect += (double)(float(NM) - sq);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = base[R * (l + LQ * j) + r];
+      if constexpr (R > 1) __syncthreads();  // regions are shared across groups
+      else __syncwarp();
+      F::fwd(v, base, r, tw, twr, l);
+      store_spectrum(v);
+      continue;
+    }
+
+    if (MODE == ROW_INV_PROJECT_FWD && tid < C) {
+      // the old field of this group's rows, wanted after the inverse transform
+      const long long nr = rows - row0 < RB ? rows - row0 : RB;
+      bulk_prefetch_l2(A + tid * P + row0 * N, (unsigned)(nr * N * sizeof(float)));
+    } else if (tid >= 32 && tid < 32 + RB * Q && (persistent || ahead > 0)) {
+      // the spectrum rows of the group this block (or a block of a later
+      // wave) takes next
+      const long long rn = (persistent ? row0 + gstep * RB : row0 + (long long)ahead * RB) + (tid - 32) / Q;
+      const int qq = (tid - 32) % Q;
+      if (rn < rows) {
+        const int cols = qq == Q - 1 ? g.xh : N;
+        bulk_prefetch_l2(W + qq * P + rn * N, (unsigned)((cols * sizeof(float2) + 15) & ~15u));
+      }
+    }
+
+    // inverse modes: the spectrum rows straight into registers (coalesced); a
+    // Hermitian last plane supplies columns k > N/2 as conj(column N - k)
+    const float2* wrow = W + q * P + off;  // this sequence's spectrum row
+    if (!live) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = float2{0.f, 0.f};
+    } else if (!mirror) {  // warp-uniform: one address per element, constant offsets
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = wrow[l + M * r + LQ * j];
     } else {
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const int k = l + LQ * j + M * r;
-        if (k < g.xh) wdst[k] = u[j];
+        const bool up = 2 * k > N;
+        float2 z = wrow[up ? N - k : k];
+        z.y = up ? -z.y : z.y;
+        v[j] = z;
       }
     }
-  };
+    F::inv(v, base, r, tw, twr, l);
 
-  if (MODE == ROW_FWD) {
-    // per point: load all channels, accumulate n - |A|^2, park the planes
-    double defect = 0.0;
+    if (MODE == ROW_INV_OUT) {
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int x = R * (l + LQ * j) + r;
+          A[(2 * q) * P + off + x] = v[j].x;
+          if (2 * q + 1 < C) A[(2 * q + 1) * P + off + x] = v[j].y;
+        }
+      }
+      continue;
+    }
+
+    // ROW_INV_PROJECT_FWD
+    if constexpr (R > 1) __syncthreads();  // every group's transposes are done: the regions hold points now
+#pragma unroll
+    for (int j = 0; j < E; ++j) base[R * (l + LQ * j) + r] = v[j];
+    if (tid == 0) s_nfb = 0;
+    __syncthreads();
     for (int p = tid; p < RB * N; p += NT) {
       const int rw = p / N, x = p - rw * N;
       if (row0 + rw >= rows) continue;
-      const long long o = (row0 + rw) * N + x;
-      float sq = 0.f;
+      // issued first, used last: the loads overlap the projection (the rows
+      // were prefetched to L2 at the start of the group)
+      float old[C];
+      {
+        const float* src = A + (row0 + rw) * N + x;
+#pragma unroll
+        for (int c = 0; c < C; ++c, src += P) old[c] = *src;
+      }
+      const long long ro = (row0 + rw) * N;
+      float2* pt = sm + rw * Q * PS + x;
+      float m[C];
 #pragma unroll
       for (int qq = 0; qq < Q; ++qq) {
-        const float re = Ain[(2 * qq) * P + o];
-        const float im = (2 * qq + 1 < C) ? Ain[(2 * qq + 1) * P + o] : 0.f;
-        sm[(rw * Q + qq) * PS + x] = float2{re, im};
-        sq += re * re + im * im;
+        const float2 z = pt[qq * PS];
+        m[2 * qq] = z.x;
+        if (2 * qq + 1 < C) m[2 * qq + 1] = z.y;
       }
-      defect += (double)(float(NM) - sq);
+      // finite entries have a finite sum of squares (up to overflow, which
+      // the entry-wise test below settles)
+      float nx = 0.f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) nx += m[c] * m[c];
+      bool fin = isfinite(nx);
+      if (!fin) {
+        fin = true;
+#pragma unroll
+        for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
+      }
+      ps.nonfinite += fin ? 0 : 1;
+      float b[C];
+      float sg;
+      if (!project_point<NM>(m, b, sg, fb_sigma) && fin) {
+        const int slot = atomicAdd(&s_nfb, 1);
+        if (slot < kFallbackCap) {
+          fbX[slot] = p;
+#pragma unroll
+          for (int c = 0; c < C; ++c) fbM[slot * C + c] = m[c];
+          continue;
+        }
+        sg = project_point_f64<NM>(m, b);
+        ps.fallback += 1;
+      }
+      finish_point<NM>(A, P, ro, x, old, b, sg, pt, PS, ps);
+    }
+    if (NM >= 2) {
+      // the FP64 re-projections collected above, spread over the block
+      __syncthreads();
+      const int nf = min(s_nfb, kFallbackCap);
+      for (int k = tid; k < nf; k += NT) {
+        const int p = fbX[k];
+        const int rw = p / N, x = p - rw * N;
+        const long long ro = (row0 + rw) * N;
+        float m[C], b[C], old[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          m[c] = fbM[k * C + c];
+          old[c] = A[c * P + ro + x];
+        }
+        const float sg = project_point_f64<NM>(m, b);
+        ps.fallback += 1;
+        finish_point<NM>(A, P, ro, x, old, b, sg, sm + rw * Q * PS + x, PS, ps);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = base[R * (l + LQ * j) + r];
-    if constexpr (R > 1) __syncthreads();  // regions are shared across groups
+    if constexpr (R > 1) __syncthreads();
     else __syncwarp();
     F::fwd(v, base, r, tw, twr, l);
     store_spectrum(v);
-    if (sp.do_stats) {
-      const double tot = block_sum(defect, redd);
-      double all;
-      if (grid_sum(tot, sp.rb, redd, &s_flag, &all) && tid == 0) sp.st->defect = all;
-    }
+  }
+
+  if (!sp.do_stats || MODE == ROW_INV_OUT) return;
+  if (MODE == ROW_FWD) {
+    const double tot = block_sum(defect, redd);
+    double all;
+    if (grid_sum(tot, sp.rb, redd, &s_flag, &all) && tid == 0) sp.st->defect = all;
     return;
   }
-
-  if (MODE == ROW_INV_PROJECT_FWD && tid < C) {
-    // the old field of this block's rows, wanted after the inverse transform
-    const long long nr = rows - row0 < RB ? rows - row0 : RB;
-    bulk_prefetch_l2(A + tid * P + row0 * N, (unsigned)(nr * N * sizeof(float)));
-  } else if (ahead > 0 && tid >= 32 && tid < 32 + RB * Q) {
-    // the spectrum rows of a block of a later wave
-    const long long rn = row0 + (long long)ahead * RB + (tid - 32) / Q;
-    const int qq = (tid - 32) % Q;
-    if (rn < rows) {
-      const int cols = qq == Q - 1 ? g.xh : N;
-      bulk_prefetch_l2(W + qq * P + rn * N, (unsigned)((cols * sizeof(float2) + 15) & ~15u));
-    }
-  }
-
-  // inverse modes: the spectrum rows straight into registers (coalesced); a
-  // Hermitian last plane supplies columns k > N/2 as conj(column N - k)
-  const bool mirror = q == Q - 1 && g.xh < N;
-  const float2* wrow = W + q * P + off;  // this sequence's spectrum row
-  if (!live) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = float2{0.f, 0.f};
-  } else if (!mirror) {  // warp-uniform: one address per element, constant offsets
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = wrow[l + M * r + LQ * j];
-  } else {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int k = l + LQ * j + M * r;
-      const bool up = 2 * k > N;
-      float2 z = wrow[up ? N - k : k];
-      z.y = up ? -z.y : z.y;
-      v[j] = z;
-    }
-  }
-  F::inv(v, base, r, tw, twr, l);
-
-  if (MODE == ROW_INV_OUT) {
-    if (live) {
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int x = R * (l + LQ * j) + r;
-        A[(2 * q) * P + off + x] = v[j].x;
-        if (2 * q + 1 < C) A[(2 * q + 1) * P + off + x] = v[j].y;
-      }
-    }
-    return;
-  }
-
-  // ROW_INV_PROJECT_FWD
-  if constexpr (R > 1) __syncthreads();  // every group's transposes are done: the regions hold points now
-#pragma unroll
-  for (int j = 0; j < E; ++j) base[R * (l + LQ * j) + r] = v[j];
-  float* fbM = reinterpret_cast<float*>(sm + wrow_nseq(N, NM) * PS);
-  int* fbX = reinterpret_cast<int*>(fbM + kFallbackCap * C);
-  if (tid == 0) s_nfb = 0;
-  __syncthreads();
-  PointStats<float> ps;
-  for (int p = tid; p < RB * N; p += NT) {
-    const int rw = p / N, x = p - rw * N;
-    if (row0 + rw >= rows) continue;
-    // issued first, used last: the loads overlap the projection (the rows
-    // were prefetched to L2 at the start of the block)
-    float old[C];
-    {
-      const float* src = A + (row0 + rw) * N + x;
-#pragma unroll
-      for (int c = 0; c < C; ++c, src += P) old[c] = *src;
-    }
-    const long long ro = (row0 + rw) * N;
-    float2* pt = sm + rw * Q * PS + x;
-    float m[C];
-#pragma unroll
-    for (int qq = 0; qq < Q; ++qq) {
-      const float2 z = pt[qq * PS];
-      m[2 * qq] = z.x;
-      if (2 * qq + 1 < C) m[2 * qq + 1] = z.y;
-    }
-    // finite entries have a finite sum of squares (up to overflow, which
-    // the entry-wise test below settles)
-    float nx = 0.f;
-#pragma unroll
-    for (int c = 0; c < C; ++c) nx += m[c] * m[c];
-    bool fin = isfinite(nx);
-    if (!fin) {
-      fin = true;
-#pragma unroll
-      for (int c = 0; c < C; ++c) fin = fin && isfinite(m[c]);
-    }
-    ps.nonfinite += fin ? 0 : 1;
-    float b[C];
-    float sg;
-    if (!project_point<NM>(m, b, sg, fb_sigma) && fin) {
-      const int slot = atomicAdd(&s_nfb, 1);
-      if (slot < kFallbackCap) {
-        fbX[slot] = p;
-#pragma unroll
-        for (int c = 0; c < C; ++c) fbM[slot * C + c] = m[c];
-        continue;
-      }
-      sg = project_point_f64<NM>(m, b);
-      ps.fallback += 1;
-    }
-    finish_point<NM>(A, P, ro, x, old, b, sg, pt, PS, ps);
-  }
-  if (NM >= 2) {
-    // the FP64 re-projections collected above, spread over the block
-    __syncthreads();
-    const int nf = min(s_nfb, kFallbackCap);
-    for (int k = tid; k < nf; k += NT) {
-      const int p = fbX[k];
-      const int rw = p / N, x = p - rw * N;
-      const long long ro = (row0 + rw) * N;
-      float m[C], b[C], old[C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        m[c] = fbM[k * C + c];
-        old[c] = A[c * P + ro + x];
-      }
-      const float sg = project_point_f64<NM>(m, b);
-      ps.fallback += 1;
-      finish_point<NM>(A, P, ro, x, old, b, sg, sm + rw * Q * PS + x, PS, ps);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = base[R * (l + LQ * j) + r];
-  if constexpr (R > 1) __syncthreads();
-  else __syncwarp();
-  F::fwd(v, base, r, tw, twr, l);
-  store_spectrum(v);
-  if (!sp.do_stats) return;
   finalize_step_stats(g.P, g.tau, sp, ps, redd, redi, &s_flag);
 }
 
@@ -253,8 +264,10 @@ cudaError_t wrow_nm(const Geom& g, const Tables<float>& t, const float* Ain, flo
   const int blocks = (int)((rows + RB - 1) / RB);
   // a block prefetches the spectrum rows of the block one wave later
   const int ahead = blocks > resident ? resident : 0;
-  return launch_pdl(k, blocks, wrow_threads(N, NM), smem, s, g, t, Ain, A, static_cast<float2*>(W), sp,
-                    fb, ahead);
+  // persistent: one wave of blocks walks the row groups with a stride of the grid
+  const int persistent = (wrow_persistent_flag() && blocks > resident) ? 1 : 0;
+  return launch_pdl(k, persistent ? resident : blocks, wrow_threads(N, NM), smem, s, g, t, Ain, A,
+                    static_cast<float2*>(W), sp, fb, ahead, persistent);
 }
 
 template <int N>
@@ -328,6 +341,11 @@ double wrow_waves(const Geom& g) {
     case 256: return wrow_waves_n<256>(g);
     default: return 0.0;
   }
+}
+
+bool& wrow_persistent_flag() {
+  thread_local bool on = false;
+  return on;
 }
 
 bool& pdl_flag() {

@@ -211,6 +211,7 @@ int pick_tx(int nx, int cap);
 
 // FP32 passes over warp-plan axes (k_warp.cu).
 bool& pdl_flag();  // programmatic dependent launch of these passes (per host thread)
+bool& wrow_persistent_flag();  // x pass as one wave of blocks over the row groups (per host thread)
 double wrow_waves(const Geom& g);  // waves of blocks of the projecting x pass
 bool warp_plan_length(int N);
 int warp_plan_radix(int N);
