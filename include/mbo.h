@@ -91,7 +91,8 @@ typedef struct {
   int autotune;          /* 1: mbo_create times the candidate launch shapes of
                             this geometry (tile width, tile buffers, threads per
                             block of the strided and row passes, dependent
-                            launch) on a scratch
+                            launch, the x pass as one wave of blocks or one
+                            block per row group) on a scratch
                             field and keeps the fastest; the choice is cached
                             per (dims, n, dtype) for the process.  Fields set
                             explicitly above are not tuned.  Default 0.        */

@@ -442,7 +442,7 @@ void invalidate_graph(mbo_ctx* h) {
 // ---------------------------------------------------------------------------
 struct LaunchShape {
   int tx, stages, axis_threads, row_threads;
-  bool pdl;
+  bool pdl, xpers;
 };
 using TuneKey = std::tuple<int, int, int, int, int, int>;
 std::mutex g_tune_mu;
@@ -480,6 +480,7 @@ cudaError_t apply_shape(mbo_ctx* h, const LaunchShape& c) {
   h->axis_threads = c.axis_threads;
   h->row_threads = c.row_threads;
   h->pdl = c.pdl;
+  h->xpers = c.xpers;
   invalidate_graph(h);
   const Geom& g = h->g;
   cudaError_t e = h->dtype == MBO_F32 ? prepare_kernels<float>(g, h->tf, h->tx, h->axis_stages)
@@ -519,7 +520,7 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   const Geom& g = h->g;
   const mbo_config& c = h->cfg;
   const TuneKey key{g.ndim, g.nz, g.ny, g.nx, g.n, (int)h->dtype};
-  LaunchShape best{h->tx, h->axis_stages, h->axis_threads, h->row_threads, h->pdl};
+  LaunchShape best{h->tx, h->axis_stages, h->axis_threads, h->row_threads, h->pdl, h->xpers};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -580,13 +581,19 @@ mbo_status autotune(mbo_ctx* h, int maxsm) {
   const LaunchShape start = best;
   for (int t : txs)
     for (int st : stages)
-      for (int at : athreads) consider(LaunchShape{t, st, at, start.row_threads, start.pdl});
+      for (int at : athreads) consider(LaunchShape{t, st, at, start.row_threads, start.pdl, start.xpers});
   const LaunchShape mid = best;
   for (int rt : rthreads)
-    if (rt != mid.row_threads) consider(LaunchShape{mid.tx, mid.stages, mid.axis_threads, rt, mid.pdl});
-  if (!c.pdl && f32 && !net_row) {  // programmatic dependent launch on or off
-    LaunchShape alt = best;
-    alt.pdl = !alt.pdl;
+    if (rt != mid.row_threads)
+      consider(LaunchShape{mid.tx, mid.stages, mid.axis_threads, rt, mid.pdl, mid.xpers});
+  if (f32 && !net_row) {
+    if (!c.pdl) {  // programmatic dependent launch on or off
+      LaunchShape alt = best;
+      alt.pdl = !alt.pdl;
+      consider(alt);
+    }
+    LaunchShape alt = best;  // the x pass as one wave of blocks, or one block per row group
+    alt.xpers = !alt.xpers;
     consider(alt);
   }
   if (e == cudaSuccess) e = apply_shape(h, best);
