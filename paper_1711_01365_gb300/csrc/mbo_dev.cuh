@@ -1082,6 +1082,35 @@ __device__ __forceinline__ double sum_partials(const double* p, int count, doubl
   return block_sum(acc, red);
 }
 
+// Two fixed-order partial sums by one block in one pass (their loads overlap):
+// the same per-thread split and reduction tree as sum_partials, so each total
+// is bit-identical to sum_partials of its array.  At most 16 warps; red needs
+// 32 slots.
+__device__ __forceinline__ void sum_partials2(const double* p1, int n1, const double* p2, int n2,
+                                              double* red, double& s1, double& s2) {
+  double a1 = 0.0, a2 = 0.0;
+  const int n = n1 > n2 ? n1 : n2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (i < n1) a1 += __ldcg(&p1[i]);
+    if (i < n2) a2 += __ldcg(&p2[i]);
+  }
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    red[w] = a1;
+    red[16 + w] = a2;
+  }
+  __syncthreads();
+  s1 = s2 = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s1 = warp_sum((l < nw) ? red[l] : 0.0);
+    s2 = warp_sum((l < nw) ? red[16 + l] : 0.0);
+  }
+}
+
 // Deterministic grid-wide sum of one double per block (thread 0's v).  Up to
 // kReduceOneLevel blocks, the last block to arrive sums all partials in index
 // order (one round of fence and counter); larger grids take two levels: blocks are grouped by kReduceGroup consecutive indices; the last
@@ -1090,15 +1119,20 @@ __device__ __forceinline__ double sum_partials(const double* p, int count, doubl
 // true in exactly one block, whose thread 0 receives the total.  The
 // counters return to zero.
 __device__ __forceinline__ bool grid_sum(double v, const ReduceBufs& rb, double* red, int* s_flag,
-                                         double* total) {
+                                         double* total, const double* extra = nullptr,
+                                         const unsigned* extra_n = nullptr, double* extra_total = nullptr) {
   const unsigned nb = gridDim.x, b = blockIdx.x;
   if (nb <= kReduceOneLevel) {
     // one level: the last block to arrive sums every partial in index order
+    // (and, when asked, another partial array in the same pass)
     if (threadIdx.x == 0) rb.part[b] = v;
     if (!last_to_arrive(&rb.gcount[0], nb, s_flag)) return false;
-    const double t = sum_partials(rb.part, (int)nb, red);
+    double t, te = 0.0;
+    if (extra) sum_partials2(rb.part, (int)nb, extra, (int)*extra_n, red, t, te);
+    else t = sum_partials(rb.part, (int)nb, red);
     if (threadIdx.x == 0) {
       *total = t;
+      if (extra) *extra_total = te;
       rb.gcount[0] = 0;
     }
     return true;
@@ -1115,8 +1149,10 @@ __device__ __forceinline__ bool grid_sum(double v, const ReduceBufs& rb, double*
   }
   if (!last_to_arrive(rb.done, ngroups, s_flag)) return false;
   const double t = sum_partials(rb.gpart, (int)ngroups, red);
+  const double te = extra ? sum_partials(extra, (int)*extra_n, red) : 0.0;
   if (threadIdx.x == 0) {
     *total = t;
+    if (extra) *extra_total = te;
     *rb.done = 0;
   }
   return true;

@@ -226,11 +226,11 @@ __device__ __forceinline__ void finalize_step_stats(long long P, double tau, con
     if (nfin) atomicAdd(&sp.st->nonfinite, (unsigned long long)nfin);
     if (nfb) atomicAdd(&sp.st->fallback, (unsigned long long)nfb);
   }
-  double all;
-  if (grid_sum(dsum, sp.rb, redd, s_flag, &all)) {
-    // deferred energy of this step's input: the multiplier pass's partials
-    // (block order) with the defect of A_s, still in st->defect
-    const double esum = sp.epart ? sum_partials(sp.epart, (int)sp.st->nep, redd) : 0.0;
+  double all, esum = 0.0;
+  // deferred energy of this step's input: the multiplier pass's partials
+  // (block order), summed by the last block with the defects; the defect of
+  // A_s is still in st->defect
+  if (grid_sum(dsum, sp.rb, redd, s_flag, &all, sp.epart, sp.epart ? &sp.st->nep : nullptr, &esum)) {
     if (tid == 0) {
       RunState* st = sp.st;
       const long long slot = st->step & (kRing - 1);
