@@ -18,10 +18,10 @@
 namespace mbo {
 namespace {
 
-template <int NM, int MODE, int N>
+template <int NM, int MODE, int N, bool PERS>
 __global__ void __launch_bounds__(wrow_threads(N, NM), wrow_minb(N, NM))
 k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2* W, StatsPtrs sp,
-       float fb_sigma, int ahead, int persistent) {
+       float fb_sigma, int ahead) {
   constexpr int R = w_r(N), M = w_m(N), LQ = w_lq(N), RB = wrow_rb(N);
   using F = WarpFFTR<M, LQ, R>;
   constexpr int C = NM * NM, Q = (C + 1) / 2, E = F::E, RS = F::RS, NT = wrow_threads(N, NM);
@@ -52,10 +52,10 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
   PointStats<float> ps;  // projection mode: over all of the block's rows
   double defect = 0.0;   // forward mode
 
-  // Row groups of this block: its own index, or with `persistent` the groups
+  // Row groups of this block: its own index, or with PERS the groups
   // blockIdx.x, blockIdx.x + gridDim.x, ... (a grid of one wave).
-  const long long gstep = persistent ? gridDim.x : ngroups;
-  for (long long gi = blockIdx.x; gi < ngroups; gi += gstep) {
+  const long long gstep = PERS ? (long long)gridDim.x : ngroups;
+  auto do_group = [&](long long gi) {
     const long long row0 = gi * RB;
     const bool live = seq < RB * Q && row0 + row < rows;  // a whole sequence is live or not
     const long long off = (row0 + row) * N;
@@ -75,7 +75,6 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
         }
       }
     };
-    if (gi != blockIdx.x) __syncthreads();  // the previous group's regions are free
 
     if (MODE == ROW_FWD) {
       // per point: load all channels, accumulate n - |A|^2, park the planes
@@ -100,17 +99,17 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
       else __syncwarp();
       F::fwd(v, base, r, tw, twr, l);
       store_spectrum(v);
-      continue;
+      return;
     }
 
     if (MODE == ROW_INV_PROJECT_FWD && tid < C) {
       // the old field of this group's rows, wanted after the inverse transform
       const long long nr = rows - row0 < RB ? rows - row0 : RB;
       bulk_prefetch_l2(A + tid * P + row0 * N, (unsigned)(nr * N * sizeof(float)));
-    } else if (tid >= 32 && tid < 32 + RB * Q && (persistent || ahead > 0)) {
+    } else if (tid >= 32 && tid < 32 + RB * Q && (PERS || ahead > 0)) {
       // the spectrum rows of the group this block (or a block of a later
       // wave) takes next
-      const long long rn = (persistent ? row0 + gstep * RB : row0 + (long long)ahead * RB) + (tid - 32) / Q;
+      const long long rn = (PERS ? row0 + gstep * RB : row0 + (long long)ahead * RB) + (tid - 32) / Q;
       const int qq = (tid - 32) % Q;
       if (rn < rows) {
         const int cols = qq == Q - 1 ? g.xh : N;
@@ -148,7 +147,7 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
           if (2 * q + 1 < C) A[(2 * q + 1) * P + off + x] = v[j].y;
         }
       }
-      continue;
+      return;
     }
 
     // ROW_INV_PROJECT_FWD
@@ -230,6 +229,14 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
     else __syncwarp();
     F::fwd(v, base, r, tw, twr, l);
     store_spectrum(v);
+  };
+  if constexpr (PERS) {
+    for (long long gi = blockIdx.x; gi < ngroups; gi += gstep) {
+      if (gi != blockIdx.x) __syncthreads();  // the previous group's regions are free
+      do_group(gi);
+    }
+  } else {
+    do_group(blockIdx.x);
   }
 
   if (!sp.do_stats || MODE == ROW_INV_OUT) return;
@@ -245,11 +252,15 @@ k_wrow(Geom g, Tables<float> t, const float* __restrict__ Ain, float* A, float2*
 template <int NM, int MODE, int N>
 cudaError_t wrow_nm(const Geom& g, const Tables<float>& t, const float* Ain, float* A, void* W,
                     const StatsPtrs& sp, float fb, cudaStream_t s, bool prepare_only) {
-  auto k = k_wrow<NM, MODE, N>;
-  static size_t done = 0;
+  // the one-wave form is instantiated for the projecting pass only
+  constexpr bool CAN_PERS = MODE == ROW_INV_PROJECT_FWD;
+  auto k = k_wrow<NM, MODE, N, false>;
+  auto kp = k_wrow<NM, MODE, N, CAN_PERS>;
+  static size_t done = 0, done_p = 0;
   static int resident = 0;  // blocks of this kernel that fit on the device at once
   const size_t smem = wrow_smem_bytes(g, N, MODE == ROW_INV_PROJECT_FWD);
   cudaError_t e = set_smem_once(k, smem, done);
+  if (e == cudaSuccess && CAN_PERS) e = set_smem_once(kp, smem, done_p);
   if (e != cudaSuccess) return e;
   if (!resident) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -265,9 +276,11 @@ cudaError_t wrow_nm(const Geom& g, const Tables<float>& t, const float* Ain, flo
   // a block prefetches the spectrum rows of the block one wave later
   const int ahead = blocks > resident ? resident : 0;
   // persistent: one wave of blocks walks the row groups with a stride of the grid
-  const int persistent = (wrow_persistent_flag() && blocks > resident) ? 1 : 0;
-  return launch_pdl(k, persistent ? resident : blocks, wrow_threads(N, NM), smem, s, g, t, Ain, A,
-                    static_cast<float2*>(W), sp, fb, ahead, persistent);
+  if (CAN_PERS && wrow_persistent_flag() && blocks > resident)
+    return launch_pdl(kp, resident, wrow_threads(N, NM), smem, s, g, t, Ain, A, static_cast<float2*>(W),
+                      sp, fb, 0);
+  return launch_pdl(k, blocks, wrow_threads(N, NM), smem, s, g, t, Ain, A, static_cast<float2*>(W), sp,
+                    fb, ahead);
 }
 
 template <int N>
@@ -306,7 +319,7 @@ size_t wrow_smem_bytes(const Geom& g, int N, bool fallback) {
 
 namespace {
 template <int NM, int N> double wrow_waves_nm(const Geom& g) {
-  auto k = k_wrow<NM, ROW_INV_PROJECT_FWD, N>;
+  auto k = k_wrow<NM, ROW_INV_PROJECT_FWD, N, false>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
