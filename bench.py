@@ -442,7 +442,7 @@ def bench_3d(torch, M, name, steps, warmup, hbm, peak_kind):
     w_bytes = ((Q - 1) * nx + xh) * (P // nx) * 2 * 4
     S = C * P * 4
     pt = {k: v[0] / 1e3 / max(v[1], 1) for k, v in passes.items() if v[1]}
-    # SURVEY 8(d): a 3-D step moves 8S algorithmic bytes (four passes, each reading and writing the field's bytes)
+    # a 3-D step moves 8S algorithmic bytes (four passes, each reading and writing the field's bytes)
     return {"workload": f"3-D flat torus {'x'.join(map(str, dims))}, n=3, FP32, tau=2h^2",
             "value": P / t, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * t, "dtype": "f32",
             "roofline": {"bound": "hbm", "achieved": 8 * S / t / 1e9, "peak": hbm, "unit": "GB/s",
