@@ -142,7 +142,11 @@ def test_strided_pass_shapes_change_nothing(M, dims):
     ref = None
     for tx in (8, 16, 4):
         for stages in (1, 2, 3):
-            h = M.Mbo(dims, n, tau, "f32", axis_tx=tx, axis_stages=stages)
+            try:
+                h = M.Mbo(dims, n, tau, "f32", axis_tx=tx, axis_stages=stages)
+            except M.MboError as e:  # a shape whose buffers exceed shared memory is refused
+                assert e.status == 2 and tx == 16 and stages > 1, (tx, stages, e)
+                continue
             A = A0.clone()
             r1 = h.step(A, want_stats=True)
             r2 = h.step(A, flags=M.MBO_STEP_CONTINUE, want_stats=True)
