@@ -394,7 +394,7 @@ def bench_c1(torch, M, steps):
 
     F, n, tau = I.config_field("C1")
     A0 = O.project(F, n)
-    h = M.Mbo(F.shape[1:], n, tau, "f64")
+    h = M.Mbo(F.shape[1:], n, tau, "f64", autotune=1)  # launch shapes timed at creation
     t = torch.tensor(A0, dtype=torch.float64, device="cuda")
     h.run(t, 10, -1.0)  # warm-up (captures the step graph)
     s = torch.cuda.current_stream()
@@ -411,7 +411,8 @@ def bench_c1(torch, M, steps):
             "value": P * r["steps"] / (ms / 1e3), "unit": UNIT, "steps": int(r["steps"]),
             "us_per_step": 1e3 * ms / r["steps"], "dtype": "f64",
             "note": "mbo_run_until_stationary with tol < 0 (no early stop); includes the run's "
-                    "host polls of the step records; the field fits in L2 (launch-latency bound)"}
+                    "host polls of the step records; launch shapes autotuned; the field fits in L2 "
+                    "(latency bound: 128 rows of FP64 work per pass)"}
 
 
 def bench_3d(torch, M, name, steps, warmup, hbm, peak_kind):
