@@ -810,16 +810,15 @@ def run_surface(args, ws, rank, local):
     vol_ms = v0.elapsed_time(v1) / args.steps
     value, t = job_throughput(nq, args.steps, ms / 1e3, device="cuda")
     # spreading: W^3 multiply-adds per source and channel (2 flops each) on the
-    # FP32 vector units: 152 SMs x 128 lanes x 2 flops x the SM clock
+    # FP32 vector units, against the measured FFMA rate of this device
     W = prm["width"]
     flops = 2.0 * nq * W ** 3 * n * n
     sp_ms = passes["spread"][0] / max(passes["spread"][1], 1)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak = M.mbo_measure_fma_peaks()["fp32"]
     achieved = flops / (sp_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "spread", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock",
+                "peak_kind": "measured (mbo_measure_fma_peaks, FFMA chains)",
                 "traffic": None, "alg_flops_per_launch": flops, "launch_us": sp_ms * 1e3,
                 "passes_us": {k: 1e3 * v[0] / max(v[1], 1) for k, v in passes.items() if v[1]}}
     if rank == 0:
